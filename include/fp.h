@@ -1,0 +1,207 @@
+/*
+ * fp.h -- C ABI of the GB300 fingerprint-filtered keyword matcher.
+ *
+ * Method: Cislak and Grabowski, "Lightweight Fingerprints for Fast Approximate
+ * Keyword Matching Using Bitwise Operations" (arXiv 1711.08475).  A pattern P
+ * is compared with every string of a collection D = [S_1 .. S_|D|] (Sec. 1,
+ * keyword / dictionary matching) and every index i with D(P, S_i) <= k is
+ * reported, D being the Hamming or the Levenshtein distance (Sec. 1).  Each
+ * string carries a fixed-size fingerprint (Sec. 3); a pair is rejected
+ * without looking at the strings when ceil(F_D / 2) > k (Eq. 1, Sec. 3.3), and
+ * only the remaining pairs are verified explicitly (Sec. 3, Sec. 4).
+ *
+ * All entry points return 0 (FP_OK) or a negative error code; none aborts or
+ * traps.  fp_strerror() describes a code; fp_last_error() gives the text of
+ * the most recent failure on the calling thread (including the CUDA error
+ * string for FP_E_CUDA).  Strings are byte arrays with explicit lengths given
+ * by CSR offsets (string i is chars[offsets[i] .. offsets[i+1]) ); they are
+ * not NUL-terminated and may contain any byte.  Lengths must be 0..255.
+ *
+ * Pointers: "host" arguments are ordinary CPU memory (pinned memory makes the
+ * copies asynchronous); "host or device" arguments are accepted from either
+ * side, the library asks the CUDA runtime which one it is.  The caller keeps
+ * ownership of every input; the library copies what it needs before the call
+ * returns.  Objects returned through an out-pointer are owned by the library
+ * until the matching *_free call.
+ *
+ * Streams: cuda_stream is a cudaStream_t (NULL = the legacy default stream).
+ * Device work of a call is ordered on that stream.
+ */
+#ifndef FP_H
+#define FP_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FP_API __attribute__((visibility("default")))
+#else
+#define FP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------- */
+#define FP_OK 0
+#define FP_E_INVAL (-1)       /* null pointer, bad size, width, k, length > 255, offsets not monotone */
+#define FP_E_UNSUPPORTED (-2) /* a (fingerprint type, metric) pair the bound does not hold for, or a layout that does not fit the width */
+#define FP_E_NOMEM (-3)       /* a device or host allocation failed */
+#define FP_E_CUDA (-4)        /* a CUDA runtime call failed; fp_last_error() has the CUDA message */
+#define FP_E_TIMEOUT (-5)     /* a bounded wait ran out (serving loop) */
+#define FP_E_OVERFLOW (-6)    /* a fixed-capacity buffer (captured plan) was too small; counts are still exact */
+
+/* ---- fingerprint types (Sec. 3) ----------------------------------------- */
+/* FP_OCC: bit q set iff a symbol mapped to q occurs (Sec. 3, "Occurrence").
+ * FP_OCC_HALVED: occurrence in S[0, floor(n/2)) at bit 2q and in the rest at
+ *   bit 2q+1 (Sec. 3, "Occurrence halved"); sound for Hamming only.
+ * FP_COUNT: saturating count min(c, 2^b - 1) of the symbols mapped to q in
+ *   bits [b q, b q + b) (Sec. 3, "Count").  Stored reflected-Gray coded: with
+ *   the paper's plain binary code one edit can change F_D by 3 or 4 (aa vs ab,
+ *   aab vs abb), which breaks Theorem 1; with a Gray code every +-1 step of a
+ *   counter flips one bit, so Theorem 1 and Eq. 1 hold.
+ * FP_POS: 0-indexed first position of the symbol mapped to field j,
+ *   saturated at 2^p - 1 (also meaning absent), in bits [p j, p j + p); the
+ *   leftover W mod p bits are occurrence bits (Sec. 3, "Position");
+ *   Hamming only (Theorem 2). */
+typedef enum { FP_OCC = 0, FP_OCC_HALVED = 1, FP_COUNT = 2, FP_POS = 3 } fp_type;
+
+/* Distances of Sec. 1. */
+typedef enum { FP_HAM = 0, FP_LEV = 1 } fp_metric;
+
+/* Symbol sets of Sec. 3: most frequent, least frequent, half of each; or a
+ * caller-given map (e.g. a learned one).  Frequencies are byte counts over
+ * the whole dictionary; ties go to the smaller byte value. */
+typedef enum { FP_SET_COMMON = 0, FP_SET_RARE = 1, FP_SET_MIXED = 2, FP_SET_CUSTOM = 3 } fp_symset;
+
+typedef struct {
+    int32_t set;               /* fp_symset; default FP_SET_COMMON */
+    int32_t count_bits;        /* b for FP_COUNT, 1..8; 0 = default 2 (Sec. 4) */
+    int32_t pos_bits;          /* p for FP_POS, 1..8; 0 = default 3 (Sec. 4) */
+    int32_t reserved;
+    const int8_t *custom_map;  /* host, [256]: field of each byte value or -1; only for FP_SET_CUSTOM */
+} fp_build_opts;
+
+/* Query execution forms. */
+typedef enum {
+    FP_MODE_TILED = 0, /* query fingerprints of a tile staged in shared memory, dictionary fingerprints streamed once per tile */
+    FP_MODE_PLAIN = 1, /* one query per warp, every dictionary fingerprint read once per query: the plain GPU scan */
+    FP_MODE_FUSED = 2  /* tiled filter with verification done inside the same persistent kernel */
+} fp_mode;
+
+typedef struct {
+    int32_t mode;            /* fp_mode; default FP_MODE_TILED */
+    int32_t tile_queries;    /* queries per block for FP_MODE_TILED / FUSED; 0 = autotuned / default */
+    int32_t words_per_thread;/* dictionary fingerprints per thread per tile, 4 or 8; 0 = default */
+    int32_t reserved;
+} fp_query_opts;
+
+typedef struct {
+    int64_t n_queries;
+    int64_t pairs;        /* eligible (query, word) pairs: equal length (Ham) or lengths within k (Lev) */
+    int64_t survivors;    /* pairs not rejected by Eq. 1 */
+    int64_t matches;      /* pairs with D <= k */
+    int64_t filter_launches;
+    float ms_prepare;     /* copy-in, bucketing, query fingerprints, tile plan */
+    float ms_filter;      /* fingerprint filter kernel(s) */
+    float ms_verify;      /* Hamming / Levenshtein verification */
+    float ms_emit;        /* sort and CSR */
+    float ms_total;       /* whole call on the device, copy-in included */
+} fp_stats;
+
+typedef struct {
+    int64_t n_words;
+    int32_t type, width_bits, count_bits, pos_bits;
+    int32_t n_pos;        /* position fields (FP_POS) */
+    int32_t sigma;        /* tracked fields */
+    int64_t bucket_count[256]; /* words per length */
+    int64_t device_bytes; /* device memory held by the index */
+} fp_index_info;
+
+typedef struct fp_index fp_index;
+typedef struct fp_result fp_result;
+
+/* ---- build (Sec. 3.2 construction, Sec. 3.4 storage) -------------------- */
+/* Copies the dictionary to the device, buckets it by length (stable: within a
+ * bucket words keep ascending index order), chooses the symbol map (Sec. 3
+ * symbol sets) and builds one fingerprint per word (Sec. 3.2).
+ *   chars, offsets: host or device; offsets[0] == 0, non-decreasing,
+ *     n_words + 1 entries, every length <= 255.
+ *   type: fp_type; width_bits: 16 or 32.
+ *   opts: NULL for defaults.
+ * Errors: FP_E_INVAL (bad pointer/size/width/offsets/length),
+ * FP_E_UNSUPPORTED (layout does not fit: b*1 > W, p*1 > W), FP_E_NOMEM,
+ * FP_E_CUDA.  Synchronises cuda_stream before returning. */
+FP_API int fp_build(const uint8_t *chars, const int64_t *offsets, int64_t n_words, int type, int width_bits,
+             const fp_build_opts *opts, void *cuda_stream, fp_index **out);
+
+/* ---- query (Sec. 3.3 comparison, Eq. 1, Sec. 4 verification) ------------ */
+/* For every pattern q, the ascending original indices i with D(P_q, S_i) <= k
+ * (Sec. 1).  The query fingerprint is built once per pattern (Sec. 4) and
+ * compared with every word of equal length (Ham) or of length within k (Lev).
+ *   chars, offsets: host or device, same rules as fp_build.
+ *   k: 0..15; metric: fp_metric.
+ *   opts: NULL for FP_MODE_TILED with the tuned tile.
+ * Errors: FP_E_INVAL, FP_E_UNSUPPORTED (FP_OCC_HALVED or FP_POS index with
+ * FP_LEV: Eq. 1 does not hold for them), FP_E_NOMEM, FP_E_CUDA.
+ * Synchronises cuda_stream once at the end (to size the result). */
+FP_API int fp_query(fp_index *ix, const uint8_t *chars, const int64_t *offsets, int64_t n_queries, int k,
+             int metric, void *cuda_stream, fp_result **out);
+FP_API int fp_query_ex(fp_index *ix, const uint8_t *chars, const int64_t *offsets, int64_t n_queries, int k,
+                int metric, const fp_query_opts *opts, void *cuda_stream, fp_result **out);
+
+/* ---- results ------------------------------------------------------------ */
+/* CSR of match lists: row_ptr[n_queries + 1] (int64) and idx[row_ptr[n]]
+ * (int32, strictly ascending within a row; duplicate dictionary strings are
+ * separate indices).  on_device = 1 returns device pointers owned by the
+ * result; 0 returns host copies owned by the result (copied on first use). */
+FP_API int fp_result_csr(fp_result *r, const int64_t **row_ptr, const int32_t **idx, int on_device);
+FP_API int fp_result_stats(const fp_result *r, fp_stats *s);
+FP_API void fp_result_free(fp_result *r);
+
+/* ---- index utilities ---------------------------------------------------- */
+FP_API int fp_index_info_get(const fp_index *ix, fp_index_info *info);
+/* The symbol map in use: map[c] = field of byte c or -1 (host, [256]). */
+FP_API int fp_index_map(const fp_index *ix, int8_t *map_out);
+/* Replaces the symbol map (Sec. 3.2: the c -> q mapping) and rebuilds every
+ * dictionary fingerprint on the device.  Any many-to-one map keeps Eq. 1
+ * valid for FP_OCC and FP_COUNT.  map: host, [256], values < sigma or -1. */
+FP_API int fp_set_symbol_map(fp_index *ix, const int8_t *map);
+/* Fingerprints (Sec. 3.2) of arbitrary strings under the index's type, width
+ * and map, in input order.  chars/offsets host or device; out_fp host or
+ * device, n_strings uint32 values (16-bit fingerprints zero-extended). */
+FP_API int fp_fingerprint(const fp_index *ix, const uint8_t *chars, const int64_t *offsets, int64_t n_strings,
+                   uint32_t *out_fp, void *cuda_stream);
+FP_API void fp_free(fp_index *ix);
+
+/* ---- diagnostics -------------------------------------------------------- */
+FP_API const char *fp_strerror(int code);
+FP_API const char *fp_last_error(void);
+/* Number of kernels this library has launched in the process so far. */
+FP_API int64_t fp_launch_count(void);
+/* Library version string. */
+FP_API const char *fp_version(void);
+
+/* Integer-pipe throughput probe used to state the filter's arithmetic
+ * ceiling.  No paper counterpart: it measures the GPU, not the method.
+ *   kind 0: the filter's per-pair work (XOR, population count, minimum,
+ *           compare with 2k) on register-resident operands; ops = pair tests
+ *   kind 1: independent chains of 3-input logic operations; ops = LOP3s
+ *   kind 2: independent chains of population counts; ops = POPCs
+ * Every SM runs the same number of resident blocks; cycles come from the SM
+ * clock counters, seconds from CUDA events on cuda_stream. */
+typedef struct {
+    int32_t kind;
+    int32_t sm_count;
+    double ops;
+    double seconds;
+    double ops_per_s;
+    double ops_per_clk_per_sm;
+    double sm_clock_mhz;
+} fp_probe_result;
+FP_API int fp_probe(int kind, int iters, void *cuda_stream, fp_probe_result *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FP_H */

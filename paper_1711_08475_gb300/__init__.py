@@ -1,0 +1,209 @@
+"""GB300-native fingerprint-filtered approximate keyword matching.
+
+Method: Cislak and Grabowski, arXiv 1711.08475.  The names below mirror the
+C ABI in include/fp.h one to one; this layer only turns numpy arrays / torch
+tensors into pointers and handles into objects.  All computation happens in
+libfpmatch.so (CUDA, sm_103a).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import native
+from .native import (FP_COUNT, FP_HAM, FP_LEV, FP_MODE_FUSED, FP_MODE_PLAIN, FP_MODE_TILED, FP_OCC,
+                     FP_OCC_HALVED, FP_POS, FP_SET_COMMON, FP_SET_CUSTOM, FP_SET_MIXED, FP_SET_RARE, FpError,
+                     check, load)
+
+TYPES = {"occ": FP_OCC, "occh": FP_OCC_HALVED, "count": FP_COUNT, "pos": FP_POS}
+METRICS = {"ham": FP_HAM, "lev": FP_LEV}
+SETS = {"common": FP_SET_COMMON, "rare": FP_SET_RARE, "mixed": FP_SET_MIXED, "custom": FP_SET_CUSTOM}
+MODES = {"tiled": FP_MODE_TILED, "plain": FP_MODE_PLAIN, "fused": FP_MODE_FUSED}
+
+__all__ = ["fp_build", "fp_query", "fp_query_ex", "Index", "Result", "fp_launch_count", "fp_version",
+           "fp_probe", "FpError", "TYPES", "METRICS", "SETS", "MODES"]
+
+
+def _ptr(a):
+    """(pointer, keep-alive) for a numpy array or torch tensor (host or device)."""
+    if a is None:
+        return None, None
+    if isinstance(a, np.ndarray):
+        a = np.ascontiguousarray(a)
+        return (a.ctypes.data if a.size else None), a
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            a = a.contiguous()
+        return (a.data_ptr() if a.numel() else None), a
+    raise TypeError(f"expected numpy array or torch tensor, got {type(a)}")
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+def _strings(chars, offsets):
+    if offsets is None and hasattr(chars, "chars") and hasattr(chars, "offsets"):
+        chars, offsets = chars.chars, chars.offsets
+    n = (offsets.shape[0] if hasattr(offsets, "shape") else len(offsets)) - 1
+    if isinstance(chars, np.ndarray):
+        chars = np.ascontiguousarray(chars, dtype=np.uint8)
+        if chars.size == 0:
+            chars = np.zeros(16, np.uint8)
+    if isinstance(offsets, np.ndarray):
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    return chars, offsets, n
+
+
+class Result:
+    """Per-query match lists (CSR) of one fp_query call."""
+
+    def __init__(self, handle: int, n_queries: int):
+        self._h = handle
+        self.n_queries = n_queries
+
+    def csr(self):
+        """Host copies: (row_ptr int64[n+1], idx int32[row_ptr[n]])."""
+        L = load()
+        rp, ix = ctypes.c_void_p(), ctypes.c_void_p()
+        check(L.fp_result_csr(self._h, ctypes.byref(rp), ctypes.byref(ix), 0), "fp_result_csr")
+        row_ptr = np.ctypeslib.as_array(ctypes.cast(rp, ctypes.POINTER(ctypes.c_int64)),
+                                        shape=(self.n_queries + 1,)).copy()
+        n = int(row_ptr[-1])
+        idx = (np.ctypeslib.as_array(ctypes.cast(ix, ctypes.POINTER(ctypes.c_int32)), shape=(n,)).copy()
+               if n else np.zeros(0, np.int32))
+        return row_ptr, idx
+
+    def device_csr(self):
+        """Device pointers (row_ptr, idx) owned by this result."""
+        L = load()
+        rp, ix = ctypes.c_void_p(), ctypes.c_void_p()
+        check(L.fp_result_csr(self._h, ctypes.byref(rp), ctypes.byref(ix), 1), "fp_result_csr")
+        return rp.value, ix.value
+
+    def stats(self) -> dict:
+        s = native.fp_stats()
+        check(load().fp_result_stats(self._h, ctypes.byref(s)), "fp_result_stats")
+        return s.as_dict()
+
+    def free(self):
+        if self._h:
+            load().fp_result_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Index:
+    """A dictionary resident on the GPU with one fingerprint per word."""
+
+    def __init__(self, handle: int):
+        self._h = handle
+
+    def info(self) -> dict:
+        i = native.fp_index_info()
+        check(load().fp_index_info_get(self._h, ctypes.byref(i)), "fp_index_info_get")
+        d = {n: getattr(i, n) for n, _ in i._fields_ if n != "bucket_count"}
+        d["bucket_count"] = np.array(i.bucket_count[:], dtype=np.int64)
+        return d
+
+    def symbol_map(self) -> np.ndarray:
+        m = np.zeros(256, dtype=np.int8)
+        check(load().fp_index_map(self._h, m.ctypes.data), "fp_index_map")
+        return m
+
+    def set_symbol_map(self, m):
+        m = np.ascontiguousarray(m, dtype=np.int8)
+        assert m.shape == (256,)
+        check(load().fp_set_symbol_map(self._h, m.ctypes.data), "fp_set_symbol_map")
+
+    def fingerprint(self, chars, offsets=None, stream=None) -> np.ndarray:
+        chars, offsets, n = _strings(chars, offsets)
+        out = np.zeros(max(n, 1), dtype=np.uint32)
+        cp, k1 = _ptr(chars)
+        op, k2 = _ptr(offsets)
+        check(load().fp_fingerprint(self._h, cp, op, n, out.ctypes.data, _stream(stream)), "fp_fingerprint")
+        return out[:n]
+
+    def query(self, chars, offsets=None, k: int = 1, metric: str = "ham", **kw) -> Result:
+        return fp_query_ex(self, chars, offsets, k, metric, **kw)
+
+    def free(self):
+        if self._h:
+            load().fp_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def fp_build(chars, offsets=None, fp_type: str = "occ", width: int = 32, symbol_set: str = "common",
+             count_bits: int = 2, pos_bits: int = 3, custom_map=None, stream=None) -> Index:
+    """Builds the resident index (fp_build in include/fp.h)."""
+    L = load()
+    chars, offsets, n = _strings(chars, offsets)
+    o = native.fp_build_opts()
+    o.set = SETS[symbol_set] if custom_map is None else FP_SET_CUSTOM
+    o.count_bits = count_bits
+    o.pos_bits = pos_bits
+    keep = None
+    if custom_map is not None:
+        keep = np.ascontiguousarray(custom_map, dtype=np.int8)
+        o.custom_map = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_int8))
+    cp, k1 = _ptr(chars)
+    op, k2 = _ptr(offsets)
+    h = ctypes.c_void_p()
+    check(L.fp_build(cp, op, n, TYPES[fp_type], width, ctypes.byref(o), _stream(stream), ctypes.byref(h)),
+          "fp_build")
+    return Index(h.value)
+
+
+def fp_query_ex(index: Index, chars, offsets=None, k: int = 1, metric: str = "ham", mode: str = "tiled",
+                tile_queries: int = 0, words_per_thread: int = 0, stream=None) -> Result:
+    """Match lists of a pattern batch (fp_query_ex in include/fp.h)."""
+    L = load()
+    chars, offsets, n = _strings(chars, offsets)
+    o = native.fp_query_opts()
+    o.mode = MODES[mode]
+    o.tile_queries = tile_queries
+    o.words_per_thread = words_per_thread
+    cp, k1 = _ptr(chars)
+    op, k2 = _ptr(offsets)
+    h = ctypes.c_void_p()
+    check(L.fp_query_ex(index._h, cp, op, n, k, METRICS[metric], ctypes.byref(o), _stream(stream),
+                        ctypes.byref(h)), "fp_query_ex")
+    return Result(h.value, n)
+
+
+def fp_query(index: Index, chars, offsets=None, k: int = 1, metric: str = "ham", stream=None) -> Result:
+    return fp_query_ex(index, chars, offsets, k, metric, stream=stream)
+
+
+def fp_launch_count() -> int:
+    return int(load().fp_launch_count())
+
+
+def fp_version() -> str:
+    return load().fp_version().decode()
+
+
+def fp_probe(kind: int, iters: int = 2000, stream=None) -> dict:
+    r = native.fp_probe_result()
+    check(load().fp_probe(kind, iters, _stream(stream), ctypes.byref(r)), "fp_probe")
+    return r.as_dict()

@@ -1,0 +1,503 @@
+// Length bucketing, symbol statistics and fingerprint construction.
+//
+// Sec. 3.4: the collection is preprocessed once and every word keeps one
+// fixed-size fingerprint (O(|D| F + sigma) extra space).  Here the words are
+// also grouped by length (Hamming compares only equal lengths, Levenshtein
+// only lengths within k), each bucket holding a structure of arrays: the
+// fingerprints (16- or 32-bit, 16-byte aligned rows of 8 slots), the original
+// index, the length and the byte offset of a zero-padded copy of the string
+// whose row length is a multiple of 16 bytes.
+//
+// Sec. 3.2 (construction): every fingerprint starts at zero and the string is
+// read once, left to right; a symbol c whose field is q = map[c] sets or
+// updates field q.  Sec. 3 (symbol sets): the map takes the most / least
+// frequent symbols of the collection, or half of each.
+#include "common.cuh"
+
+namespace fpk {
+
+int make_params(int type, int width, int b, int p, FpParams *o) {
+    if (width != 16 && width != 32) return FP_E_INVAL;
+    if (type < FP_OCC || type > FP_POS) return FP_E_INVAL;
+    if (b <= 0) b = 2;
+    if (p <= 0) p = 3;
+    if (b > 8 || p > 8) return FP_E_UNSUPPORTED;
+    FpParams P{};
+    P.type = type;
+    P.width = width;
+    P.b = b;
+    P.p = p;
+    switch (type) {
+        case FP_OCC: P.sigma = width; break;
+        case FP_OCC_HALVED: P.sigma = width / 2; break;
+        case FP_COUNT:
+            if (b > width) return FP_E_UNSUPPORTED;
+            P.sigma = width / b;
+            for (int q = 0; q < P.sigma; q++) P.count_top |= 1u << (b * q + b - 1);
+            break;
+        case FP_POS:
+            if (p > width) return FP_E_UNSUPPORTED;
+            P.n_pos = width / p;
+            P.sigma = P.n_pos + (width - p * P.n_pos);
+            for (int j = 0; j < P.n_pos; j++) {
+                P.pos_high |= 1u << (p * j + p - 1);
+                for (int t = 0; t < p - 1; t++) P.pos_low |= 1u << (p * j + t);
+            }
+            for (int t = p * P.n_pos; t < width; t++) P.pos_occ |= 1u << t;
+            break;
+    }
+    *o = P;
+    return FP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// fingerprint of one string, byte by byte (Sec. 3.2)
+// ---------------------------------------------------------------------------
+template <int TYPE>
+struct FpAcc {
+    uint32_t v, seen;
+    __device__ __forceinline__ void init(const FpParams &P) {
+        seen = 0;
+        v = (TYPE == FP_POS) ? (P.pos_low | P.pos_high) : 0u;
+    }
+    __device__ __forceinline__ void add(int q, int pos, int len, const FpParams &P) {
+        if (q < 0) return;
+        if (TYPE == FP_OCC) {
+            v |= 1u << q;
+        } else if (TYPE == FP_OCC_HALVED) {
+            v |= 1u << (2 * q + (pos >= (len >> 1) ? 1 : 0));
+        } else if (TYPE == FP_COUNT) {
+            uint32_t sat = (1u << P.b) - 1u;
+            uint32_t c = (v >> (P.b * q)) & sat;
+            if (c < sat) v += 1u << (P.b * q);
+        } else {
+            if (q < P.n_pos) {
+                if (!((seen >> q) & 1u)) {
+                    seen |= 1u << q;
+                    uint32_t sat = (1u << P.p) - 1u;
+                    uint32_t f = (uint32_t)pos < sat ? (uint32_t)pos : sat;
+                    v = (v & ~(sat << (P.p * q))) | (f << (P.p * q));
+                }
+            } else {
+                v |= 1u << (P.p * P.n_pos + (q - P.n_pos));
+            }
+        }
+    }
+    __device__ __forceinline__ uint32_t finish(const FpParams &P) {
+        uint32_t r = v;
+        if (TYPE == FP_COUNT) r = r ^ ((r >> 1) & ~P.count_top);  // per-field reflected Gray code
+        if (P.width == 16) r &= 0xFFFFu;
+        return r;
+    }
+};
+
+__device__ __forceinline__ void store_fp(void *fp, int width, int64_t slot, uint32_t v) {
+    if (width == 16) ((uint16_t *)fp)[slot] = (uint16_t)v;
+    else ((uint32_t *)fp)[slot] = v;
+}
+
+// ---------------------------------------------------------------------------
+// symbol statistics (Sec. 3 symbol sets)
+// ---------------------------------------------------------------------------
+__global__ void k_byte_hist(const uint8_t *__restrict__ chars, int64_t total,
+                            unsigned long long *__restrict__ counts) {
+    __shared__ uint32_t h[256];
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) h[t] = 0;
+    __syncthreads();
+    int64_t n16 = total / 16;
+    const uint4 *c16 = (const uint4 *)chars;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint4 v = c16[i];
+        uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+#pragma unroll
+            for (int s = 0; s < 32; s += 8) atomicAdd(&h[(w[j] >> s) & 0xFF], 1u);
+        }
+    }
+    if (blockIdx.x == 0)
+        for (int64_t i = n16 * 16 + threadIdx.x; i < total; i += blockDim.x) atomicAdd(&h[chars[i]], 1u);
+    __syncthreads();
+    for (int t = threadIdx.x; t < 256; t += blockDim.x)
+        if (h[t]) atomicAdd(&counts[t], (unsigned long long)h[t]);
+}
+
+// One block of 256 threads, thread c decides the field of byte c.
+__global__ void k_symbol_rank(const unsigned long long *__restrict__ counts, int set, int sigma,
+                              int8_t *__restrict__ map) {
+    __shared__ unsigned long long cnt[256];
+    __shared__ int crank[256];
+    const int c = threadIdx.x;
+    cnt[c] = counts[c];
+    __syncthreads();
+    const unsigned long long mine = cnt[c];
+    int cr = 0, rr = 0;
+    for (int o = 0; o < 256; o++) {
+        unsigned long long x = cnt[o];
+        if (x == 0) continue;
+        if (x > mine || (x == mine && o < c)) cr++;
+        if (x < mine || (x == mine && o < c)) rr++;
+    }
+    crank[c] = cr;
+    __syncthreads();
+    int field = -1;
+    if (mine > 0) {
+        if (set == FP_SET_COMMON) {
+            if (cr < sigma) field = cr;
+        } else if (set == FP_SET_RARE) {
+            if (rr < sigma) field = rr;
+        } else {
+            const int nc = (sigma + 1) / 2, nr = sigma / 2;
+            if (cr < nc) {
+                field = cr;
+            } else {
+                int r2 = 0;  // rank among the symbols not taken by the common half, least frequent first
+                for (int o = 0; o < 256; o++) {
+                    unsigned long long x = cnt[o];
+                    if (x == 0 || crank[o] < nc) continue;
+                    if (x < mine || (x == mine && o < c)) r2++;
+                }
+                if (r2 < nr) field = nc + r2;
+            }
+        }
+    }
+    map[c] = (int8_t)field;
+}
+
+int symbol_map(const uint8_t *d_chars, int64_t total, int set, int sigma, int8_t *d_map,
+               unsigned long long *d_counts, cudaStream_t st) {
+    FP_CUDA(cudaMemsetAsync(d_counts, 0, 256 * sizeof(unsigned long long), st));
+    if (total > 0) {
+        int64_t g = (total / 16 + 255) / 256;
+        int grid = (int)(g < 1 ? 1 : (g > 1024 ? 1024 : g));
+        k_byte_hist<<<grid, 256, 0, st>>>(d_chars, total, d_counts);
+        FP_LAUNCHED("k_byte_hist");
+    }
+    k_symbol_rank<<<1, 256, 0, st>>>(d_counts, set, sigma, d_map);
+    FP_LAUNCHED("k_symbol_rank");
+    return FP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// bucketing
+// ---------------------------------------------------------------------------
+__global__ void k_bin_keys(const int64_t *__restrict__ off, int64_t n, const int32_t *__restrict__ group,
+                           int nbins, uint64_t *__restrict__ keys, int32_t *__restrict__ hist,
+                           int32_t *__restrict__ err) {
+    extern __shared__ int32_t h[];
+    for (int t = threadIdx.x; t < nbins; t += blockDim.x) h[t] = 0;
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t L = off[i + 1] - off[i];
+        int g = group ? group[i] : 0;
+        int bin;
+        if (L < 0 || L > MAX_LEN || g < 0 || (int64_t)g * 256 + L >= nbins) {
+            atomicOr(err, 1);
+            bin = 0;
+        } else {
+            bin = g * 256 + (int)L;
+        }
+        keys[i] = ((uint64_t)bin << 32) | (uint64_t)i;
+        atomicAdd(&h[bin], 1);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nbins; t += blockDim.x)
+        if (h[t]) atomicAdd(&hist[t], h[t]);
+}
+
+// One block of 1024 threads: bucket starts (aligned), unaligned starts and
+// string-row bases.  tot[0] = slots, tot[1] = 16-byte row units.
+__global__ void __launch_bounds__(1024) k_plan_bins(const int32_t *__restrict__ hist, int nbins,
+                                                    int32_t *__restrict__ b_start,
+                                                    int32_t *__restrict__ b_count,
+                                                    int32_t *__restrict__ b_ustart,
+                                                    int64_t *__restrict__ b_str16,
+                                                    int64_t *__restrict__ tot) {
+    __shared__ int64_t s_a[1024], s_u[1024], s_r[1024];
+    const int t = threadIdx.x;
+    const int per = (nbins + 1023) / 1024;
+    const int lo = t * per, hi = lo + per < nbins ? lo + per : nbins;
+    int64_t a = 0, u = 0, r = 0;
+    for (int c = lo; c < hi; c++) {
+        int64_t n = hist[c];
+        a += (n + SLOT_ALIGN - 1) / SLOT_ALIGN * SLOT_ALIGN;
+        u += n;
+        r += n * (((c & 255) + 15) / 16);
+    }
+    s_a[t] = a;
+    s_u[t] = u;
+    s_r[t] = r;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        int64_t va = t >= o ? s_a[t - o] : 0, vu = t >= o ? s_u[t - o] : 0, vr = t >= o ? s_r[t - o] : 0;
+        __syncthreads();
+        s_a[t] += va;
+        s_u[t] += vu;
+        s_r[t] += vr;
+        __syncthreads();
+    }
+    int64_t ra = s_a[t] - a, ru = s_u[t] - u, rr = s_r[t] - r;
+    for (int c = lo; c < hi; c++) {
+        int64_t n = hist[c];
+        b_start[c] = (int32_t)ra;
+        b_count[c] = (int32_t)n;
+        b_ustart[c] = (int32_t)ru;
+        b_str16[c] = rr;
+        ra += (n + SLOT_ALIGN - 1) / SLOT_ALIGN * SLOT_ALIGN;
+        ru += n;
+        rr += n * (((c & 255) + 15) / 16);
+    }
+    if (t == 1023) {
+        tot[0] = s_a[1023];
+        tot[1] = s_r[1023];
+    }
+}
+
+template <int TYPE>
+__global__ void __launch_bounds__(256) k_scatter_fp(const uint64_t *__restrict__ sorted, int64_t n,
+                                                    const int64_t *__restrict__ off,
+                                                    const uint8_t *__restrict__ chars,
+                                                    const int8_t *__restrict__ map, FpParams P,
+                                                    const int32_t *__restrict__ b_start,
+                                                    const int32_t *__restrict__ b_ustart,
+                                                    const int64_t *__restrict__ b_str16, Bucketed B) {
+    __shared__ int8_t smap[256];
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) smap[t] = map[t];
+    __syncthreads();
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t key = sorted[p];
+        int bin = (int)(key >> 32);
+        int64_t i = (int64_t)(key & 0xffffffffu);
+        int L = bin & 255;
+        int64_t rank = p - b_ustart[bin];
+        int64_t slot = b_start[bin] + rank;
+        int64_t row16 = b_str16[bin] + rank * ((L + 15) / 16);
+        B.idx[slot] = (int32_t)i;
+        B.len[slot] = (uint8_t)L;
+        B.row16[slot] = (uint32_t)row16;
+        const uint8_t *src = chars + off[i];
+        uint4 *dst = (uint4 *)(B.str + row16 * 16);
+        FpAcc<TYPE> acc;
+        acc.init(P);
+        for (int c0 = 0; c0 < L; c0 += 16) {
+            uint32_t w[4] = {0, 0, 0, 0};
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                int pos = c0 + j;
+                if (pos < L) {
+                    uint32_t ch = src[pos];
+                    w[j >> 2] |= ch << (8 * (j & 3));
+                    acc.add(smap[ch], pos, L, P);
+                }
+            }
+            dst[c0 >> 4] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        store_fp(B.fp, P.width, slot, acc.finish(P));
+    }
+}
+
+template <int TYPE>
+__global__ void __launch_bounds__(256) k_refingerprint(Bucketed B, const int8_t *__restrict__ map,
+                                                       FpParams P) {
+    __shared__ int8_t smap[256];
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) smap[t] = map[t];
+    __syncthreads();
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < B.n_slots;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        if (B.idx[s] < 0) continue;
+        int L = B.len[s];
+        const uint4 *row = (const uint4 *)(B.str + (int64_t)B.row16[s] * 16);
+        FpAcc<TYPE> acc;
+        acc.init(P);
+        for (int c0 = 0; c0 < L; c0 += 16) {
+            uint4 v = row[c0 >> 4];
+            uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                int pos = c0 + j;
+                if (pos < L) acc.add(smap[(w[j >> 2] >> (8 * (j & 3))) & 0xFF], pos, L, P);
+            }
+        }
+        store_fp(B.fp, P.width, s, acc.finish(P));
+    }
+}
+
+template <int TYPE>
+__global__ void __launch_bounds__(256) k_fingerprint_list(const uint8_t *__restrict__ chars,
+                                                          const int64_t *__restrict__ off, int64_t n,
+                                                          const int8_t *__restrict__ map, FpParams P,
+                                                          uint32_t *__restrict__ out) {
+    __shared__ int8_t smap[256];
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) smap[t] = map[t];
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t L = off[i + 1] - off[i];
+        const uint8_t *src = chars + off[i];
+        FpAcc<TYPE> acc;
+        acc.init(P);
+        for (int64_t pos = 0; pos < L; pos++) acc.add(smap[src[pos]], (int)pos, (int)L, P);
+        out[i] = acc.finish(P);
+    }
+}
+
+static int grid_for(int64_t n, int threads = 256, int cap = 8192) {
+    int64_t g = (n + threads - 1) / threads;
+    return (int)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+int fingerprint_list(const uint8_t *d_chars, const int64_t *d_off, int64_t n, const int8_t *d_map,
+                     const FpParams &P, uint32_t *d_out, cudaStream_t st) {
+    if (n <= 0) return FP_OK;
+    int g = grid_for(n);
+    switch (P.type) {
+        case FP_OCC: k_fingerprint_list<FP_OCC><<<g, 256, 0, st>>>(d_chars, d_off, n, d_map, P, d_out); break;
+        case FP_OCC_HALVED:
+            k_fingerprint_list<FP_OCC_HALVED><<<g, 256, 0, st>>>(d_chars, d_off, n, d_map, P, d_out);
+            break;
+        case FP_COUNT: k_fingerprint_list<FP_COUNT><<<g, 256, 0, st>>>(d_chars, d_off, n, d_map, P, d_out); break;
+        default: k_fingerprint_list<FP_POS><<<g, 256, 0, st>>>(d_chars, d_off, n, d_map, P, d_out); break;
+    }
+    FP_LAUNCHED("k_fingerprint_list");
+    return FP_OK;
+}
+
+void free_bucketed(Bucketed *b, cudaStream_t st) {
+    void *ptrs[] = {b->fp, b->idx, b->len, b->row16, b->str, b->b_start, b->b_count};
+    for (void *p : ptrs) {
+        if (!p) continue;
+        if (b->stream_ordered) cudaFreeAsync(p, st);
+        else cudaFree(p);
+    }
+    *b = Bucketed{};
+}
+
+static int dev_alloc(void **p, size_t bytes, bool so, cudaStream_t st) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = so ? cudaMallocAsync(p, bytes, st) : cudaMalloc(p, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        set_error("device allocation failed");
+        return FP_E_NOMEM;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "device allocation");
+    return FP_OK;
+}
+
+int bucketize(const uint8_t *d_chars, const int64_t *d_off, int64_t n, int64_t total_chars,
+              const int32_t *d_group, int32_t n_groups, const int8_t *d_map, const FpParams &P,
+              bool so, cudaStream_t st, Bucketed *out, int32_t *d_err) {
+    Bucketed B;
+    B.stream_ordered = so;
+    B.n = n;
+    B.nbins = 256 * (n_groups < 1 ? 1 : n_groups);
+    const int nbins = B.nbins;
+    const int64_t slots_ub = n + (int64_t)(SLOT_ALIGN - 1) * nbins;
+    const int64_t str_ub = total_chars + 15 * n;
+    const size_t fpw = P.width == 16 ? 2 : 4;
+    int rc = FP_OK;
+    uint64_t *keys = nullptr, *keys2 = nullptr;
+    int32_t *hist = nullptr, *ustart = nullptr;
+    int64_t *str16 = nullptr, *tot = nullptr;
+#define ALLOC(ptr, bytes, soflag)                                      \
+    do {                                                               \
+        rc = dev_alloc((void **)&(ptr), (size_t)(bytes), soflag, st); \
+        if (rc != FP_OK) goto fail;                                    \
+    } while (0)
+    ALLOC(B.fp, (slots_ub + FP_SLACK_SLOTS) * fpw, so);
+    ALLOC(B.idx, slots_ub * 4, so);
+    ALLOC(B.len, slots_ub, so);
+    ALLOC(B.row16, slots_ub * 4, so);
+    ALLOC(B.str, str_ub + STR_SLACK, so);
+    ALLOC(B.b_start, nbins * 4, so);
+    ALLOC(B.b_count, nbins * 4, so);
+    ALLOC(keys, (n > 0 ? n : 1) * 8, true);
+    ALLOC(keys2, (n > 0 ? n : 1) * 8, true);
+    ALLOC(hist, nbins * 4, true);
+    ALLOC(ustart, nbins * 4, true);
+    ALLOC(str16, nbins * 8, true);
+    ALLOC(tot, 2 * 8, true);
+#undef ALLOC
+    {
+        cudaError_t e;
+        if ((e = cudaMemsetAsync(B.fp, 0, (slots_ub + FP_SLACK_SLOTS) * fpw, st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(B.idx, 0xFF, slots_ub * 4, st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(B.len, 0, slots_ub, st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(B.row16, 0, slots_ub * 4, st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(B.str + str_ub, 0, STR_SLACK, st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(hist, 0, nbins * 4, st)) != cudaSuccess) {
+            rc = cuda_fail(e, "cudaMemsetAsync");
+            goto fail;
+        }
+        if (n > 0) {
+            int g = grid_for(n, 256, 2048);
+            k_bin_keys<<<g, 256, nbins * sizeof(int32_t), st>>>(d_off, n, d_group, nbins, keys, hist, d_err);
+            g_launches++;
+            if ((e = cudaGetLastError()) != cudaSuccess) { rc = cuda_fail(e, "k_bin_keys"); goto fail; }
+        }
+        k_plan_bins<<<1, 1024, 0, st>>>(hist, nbins, B.b_start, B.b_count, ustart, str16, tot);
+        g_launches++;
+        if ((e = cudaGetLastError()) != cudaSuccess) { rc = cuda_fail(e, "k_plan_bins"); goto fail; }
+        if (n > 0) {
+            int bin_bits = 1;
+            while ((1 << bin_bits) < nbins) bin_bits++;
+            uint64_t *sorted = keys;
+            rc = radix_sort_u64(keys, keys2, nullptr, n, 32, 32 + bin_bits, st, &sorted);
+            if (rc != FP_OK) goto fail;
+            int g = grid_for(n, 256, 8192);
+            switch (P.type) {
+                case FP_OCC:
+                    k_scatter_fp<FP_OCC><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B.b_start, ustart, str16, B);
+                    break;
+                case FP_OCC_HALVED:
+                    k_scatter_fp<FP_OCC_HALVED><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B.b_start, ustart, str16, B);
+                    break;
+                case FP_COUNT:
+                    k_scatter_fp<FP_COUNT><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B.b_start, ustart, str16, B);
+                    break;
+                default:
+                    k_scatter_fp<FP_POS><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B.b_start, ustart, str16, B);
+                    break;
+            }
+            g_launches++;
+            if ((e = cudaGetLastError()) != cudaSuccess) { rc = cuda_fail(e, "k_scatter_fp"); goto fail; }
+        }
+    }
+    B.n_slots = slots_ub;
+    B.str_bytes = str_ub;
+    cudaFreeAsync(keys, st);
+    cudaFreeAsync(keys2, st);
+    cudaFreeAsync(hist, st);
+    cudaFreeAsync(ustart, st);
+    cudaFreeAsync(str16, st);
+    cudaFreeAsync(tot, st);
+    *out = B;
+    return FP_OK;
+fail:
+    if (keys) cudaFreeAsync(keys, st);
+    if (keys2) cudaFreeAsync(keys2, st);
+    if (hist) cudaFreeAsync(hist, st);
+    if (ustart) cudaFreeAsync(ustart, st);
+    if (str16) cudaFreeAsync(str16, st);
+    if (tot) cudaFreeAsync(tot, st);
+    free_bucketed(&B, st);
+    return rc;
+}
+
+int refingerprint(Bucketed *B, const int8_t *d_map, const FpParams &P, cudaStream_t st) {
+    if (B->n_slots <= 0) return FP_OK;
+    int g = grid_for(B->n_slots, 256, 8192);
+    switch (P.type) {
+        case FP_OCC: k_refingerprint<FP_OCC><<<g, 256, 0, st>>>(*B, d_map, P); break;
+        case FP_OCC_HALVED: k_refingerprint<FP_OCC_HALVED><<<g, 256, 0, st>>>(*B, d_map, P); break;
+        case FP_COUNT: k_refingerprint<FP_COUNT><<<g, 256, 0, st>>>(*B, d_map, P); break;
+        default: k_refingerprint<FP_POS><<<g, 256, 0, st>>>(*B, d_map, P); break;
+    }
+    FP_LAUNCHED("k_refingerprint");
+    return FP_OK;
+}
+
+}  // namespace fpk

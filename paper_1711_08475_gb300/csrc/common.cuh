@@ -1,0 +1,152 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+
+#include "fp.h"
+
+namespace fpk {
+
+// ---------------------------------------------------------------------------
+// errors and launch accounting
+// ---------------------------------------------------------------------------
+void set_error(const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+extern std::atomic<int64_t> g_launches;
+
+#define FP_CUDA(call)                                          \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return ::fpk::cuda_fail(e_, #call); \
+    } while (0)
+
+#define FP_TRY(call)               \
+    do {                           \
+        int rc_ = (call);          \
+        if (rc_ != FP_OK) return rc_; \
+    } while (0)
+
+// Counts one launch and checks the launch error.
+#define FP_LAUNCHED(name)                                       \
+    do {                                                        \
+        ::fpk::g_launches.fetch_add(1, std::memory_order_relaxed); \
+        cudaError_t e_ = cudaGetLastError();                    \
+        if (e_ != cudaSuccess) return ::fpk::cuda_fail(e_, name); \
+    } while (0)
+
+constexpr int MAX_LEN = 255;
+constexpr int SLOT_ALIGN = 8;      // bucket starts are multiples of 8 slots (16-byte fingerprint rows)
+constexpr int STR_SLACK = 512;     // readable bytes after the last string row
+constexpr int FP_SLACK_SLOTS = 8192; // readable fingerprint slots after the last bucket
+
+// ---------------------------------------------------------------------------
+// fingerprint parameters (Sec. 3, Sec. 3.2)
+// ---------------------------------------------------------------------------
+struct FpParams {
+    int32_t type;     // fp_type
+    int32_t width;    // 16 or 32
+    int32_t b;        // bits per count
+    int32_t p;        // bits per position
+    int32_t n_pos;    // position fields
+    int32_t sigma;    // tracked fields
+    uint32_t count_top;  // top bit of every count field (Gray conversion)
+    uint32_t pos_low;    // low p-1 bits of every position field
+    uint32_t pos_high;   // top bit of every position field
+    uint32_t pos_occ;    // occurrence bits above the position fields
+};
+int make_params(int type, int width, int b, int p, FpParams *out);
+
+// ---------------------------------------------------------------------------
+// a bucketed set of strings on the device (dictionary or query batch)
+// ---------------------------------------------------------------------------
+// Slots: bucket (bin) c occupies slots [start[c], start[c] + count[c]); bin c
+// holds strings of length c & 255 (bins >= 256 separate query groups).
+// Starts are multiples of SLOT_ALIGN; the gaps are padding slots with idx -1.
+struct Bucketed {
+    int32_t nbins = 0;
+    int64_t n = 0;          // strings
+    int64_t n_slots = 0;    // slots including padding
+    int64_t str_bytes = 0;  // bytes of padded rows
+    // device arrays
+    void *fp = nullptr;         // uint16 or uint32 per slot (+ FP_SLACK_SLOTS)
+    int32_t *idx = nullptr;     // original index per slot
+    uint8_t *len = nullptr;     // length per slot
+    uint32_t *row16 = nullptr;  // row byte offset / 16 per slot
+    uint8_t *str = nullptr;     // padded rows (+ STR_SLACK)
+    int32_t *b_start = nullptr; // [nbins]
+    int32_t *b_count = nullptr; // [nbins]
+    bool stream_ordered = false; // allocated with cudaMallocAsync
+};
+
+// Copies / bucketizes / fingerprints n strings.  chars and offsets are device
+// pointers.  total_chars = offsets[n].  bin of string i = group[i] * 256 + len
+// (group may be null).  map is a device int8[256].
+int bucketize(const uint8_t *d_chars, const int64_t *d_off, int64_t n, int64_t total_chars,
+              const int32_t *d_group, int32_t n_groups, const int8_t *d_map, const FpParams &fp,
+              bool stream_ordered, cudaStream_t st, Bucketed *out, int32_t *d_err);
+void free_bucketed(Bucketed *b, cudaStream_t st);
+// Rebuilds fingerprints of an existing bucketed set from its rows.
+int refingerprint(Bucketed *b, const int8_t *d_map, const FpParams &fp, cudaStream_t st);
+
+// Symbol statistics (Sec. 3 symbol sets): byte counts and the field map.
+int symbol_map(const uint8_t *d_chars, int64_t total, int set, int sigma, int8_t *d_map,
+               unsigned long long *d_counts, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// radix sort of 64-bit keys (stable LSD) and scans
+// ---------------------------------------------------------------------------
+// Sorts keys[0 .. *d_n) (or n_host if d_n is null) on bits [0, bits).
+// tmp must hold as many keys.  The sorted keys end up in *result (either keys
+// or tmp).  max_n bounds *d_n.
+int radix_sort_u64(uint64_t *keys, uint64_t *tmp, const uint64_t *d_n, int64_t max_n, int bits_lo,
+                   int bits_hi, cudaStream_t st, uint64_t **result);
+
+// ---------------------------------------------------------------------------
+// filter + verify + emit
+// ---------------------------------------------------------------------------
+struct Segment {        // one (query bucket, dictionary bucket) rectangle of pairs
+    uint32_t q_start, q_count;
+    uint32_t d_start, d_count;
+    uint32_t n_qtiles, n_dtiles;
+    uint64_t tile_begin;
+    int32_t k, metric;
+};
+
+struct QueryPlan {
+    Segment *seg = nullptr;          // device
+    int32_t max_segments = 0;
+    // device scalars (one small block)
+    uint64_t *scal = nullptr;   // [0] n_segments [1] total tiles [2] pairs [3] tile counter
+                                // [4] survivors [5] matches [6..7] spare
+};
+
+struct FilterCfg {
+    int mode;      // fp_mode
+    int tq;        // queries per tile
+    int v;         // 32-bit fingerprint words per thread (4 or 8)
+};
+
+int plan_segments(const Bucketed &q, const Bucketed &d, const int32_t *d_group_k,
+                  const int32_t *d_group_metric, int tq, int tw, QueryPlan *plan, cudaStream_t st);
+
+int launch_filter(const Bucketed &q, const Bucketed &d, const QueryPlan &plan, const FpParams &fp,
+                  const FilterCfg &cfg, uint64_t *surv, int64_t surv_cap, cudaStream_t st,
+                  int64_t *launches);
+
+int launch_verify(const Bucketed &q, const Bucketed &d, const uint64_t *surv, const uint64_t *d_n_surv,
+                  int64_t surv_cap, int k, int metric, int idx_bits, uint64_t *matches,
+                  uint64_t *d_n_matches, int64_t match_cap, cudaStream_t st);
+int tile_words(int width, int v);
+int fingerprint_list(const uint8_t *d_chars, const int64_t *d_off, int64_t n, const int8_t *d_map,
+                     const FpParams &P, uint32_t *d_out, cudaStream_t st);
+
+int build_csr(uint64_t *keys, uint64_t *tmp, const uint64_t *d_n, int64_t max_n, int q_bits, int idx_bits,
+              int64_t n_queries, int64_t *row_ptr, int32_t *idx, cudaStream_t st);
+
+int sm_count();
+
+}  // namespace fpk

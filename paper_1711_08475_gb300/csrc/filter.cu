@@ -1,0 +1,316 @@
+// The fingerprint filter (Sec. 3.3, Eq. 1) over length-bucketed tiles.
+//
+// Work is a set of segments: one query bucket (equal-length patterns of one
+// (k, metric) group) against one dictionary bucket of equal length (Hamming)
+// or of length within k (Levenshtein).  A segment is cut into tiles of
+// tq queries x tw dictionary words.  A persistent grid pops tiles from a
+// device counter; a block stages the tile's query fingerprints in shared
+// memory and every thread keeps v 32-bit words of dictionary fingerprints in
+// registers (loaded once per tile with coalesced 128-bit loads), so each
+// dictionary fingerprint read from memory serves tq queries.
+//
+// Per pair the work is one XOR and one population count (Sec. 3.3: F_D is
+// the Hamming weight of the XOR), or for position fingerprints a SWAR test of
+// which p-bit fields differ; the pair passes iff F_D <= 2k, i.e. iff
+// ceil(F_D / 2) <= k (Eq. 1).  A warp first asks whether any of its pairs
+// for the current query passed (min over its words, one vote); only then are
+// survivors compacted with ballots and appended to a global list.
+#include "common.cuh"
+
+namespace fpk {
+
+constexpr int FT_THREADS = 256;
+constexpr int FT_MAX_TQ = 256;
+
+// ---------------------------------------------------------------------------
+// tile planner: one block
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_plan_segments(
+    const int32_t *__restrict__ qb_start, const int32_t *__restrict__ qb_count, int q_nbins,
+    const int32_t *__restrict__ db_start, const int32_t *__restrict__ db_count,
+    const int32_t *__restrict__ group_k, const int32_t *__restrict__ group_metric, int tq, int tw,
+    Segment *__restrict__ seg, int max_segments, uint64_t *__restrict__ scal) {
+    __shared__ int64_t s_n[1024];
+    __shared__ uint64_t s_t[1024], s_p[1024];
+    const int t = threadIdx.x;
+    const int per = (q_nbins + 1023) / 1024;
+    const int lo = t * per, hi = lo + per < q_nbins ? lo + per : q_nbins;
+    int64_t nseg = 0;
+    uint64_t tiles = 0, pairs = 0;
+    for (int c = lo; c < hi; c++) {
+        int qc = qb_count[c];
+        if (qc <= 0) continue;
+        int g = c >> 8, n = c & 255, k = group_k[g], metric = group_metric[g];
+        int L0 = metric == FP_HAM ? n : (n - k < 0 ? 0 : n - k);
+        int L1 = metric == FP_HAM ? n : (n + k > MAX_LEN ? MAX_LEN : n + k);
+        for (int L = L0; L <= L1; L++) {
+            int dc = db_count[L];
+            if (dc <= 0) continue;
+            nseg++;
+            tiles += (uint64_t)((qc + tq - 1) / tq) * (uint64_t)((dc + tw - 1) / tw);
+            pairs += (uint64_t)qc * (uint64_t)dc;
+        }
+    }
+    s_n[t] = nseg;
+    s_t[t] = tiles;
+    s_p[t] = pairs;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        int64_t a = t >= o ? s_n[t - o] : 0;
+        uint64_t b = t >= o ? s_t[t - o] : 0, c = t >= o ? s_p[t - o] : 0;
+        __syncthreads();
+        s_n[t] += a;
+        s_t[t] += b;
+        s_p[t] += c;
+        __syncthreads();
+    }
+    int64_t si = s_n[t] - nseg;
+    uint64_t tb = s_t[t] - tiles;
+    for (int c = lo; c < hi; c++) {
+        int qc = qb_count[c];
+        if (qc <= 0) continue;
+        int g = c >> 8, n = c & 255, k = group_k[g], metric = group_metric[g];
+        int L0 = metric == FP_HAM ? n : (n - k < 0 ? 0 : n - k);
+        int L1 = metric == FP_HAM ? n : (n + k > MAX_LEN ? MAX_LEN : n + k);
+        for (int L = L0; L <= L1; L++) {
+            int dc = db_count[L];
+            if (dc <= 0) continue;
+            Segment s;
+            s.q_start = (uint32_t)qb_start[c];
+            s.q_count = (uint32_t)qc;
+            s.d_start = (uint32_t)db_start[L];
+            s.d_count = (uint32_t)dc;
+            s.n_qtiles = (uint32_t)((qc + tq - 1) / tq);
+            s.n_dtiles = (uint32_t)((dc + tw - 1) / tw);
+            s.tile_begin = tb;
+            s.k = k;
+            s.metric = metric;
+            if (si < max_segments) seg[si] = s;
+            si++;
+            tb += (uint64_t)s.n_qtiles * s.n_dtiles;
+        }
+    }
+    if (t == 1023) {
+        int64_t ns = s_n[1023];
+        scal[0] = (uint64_t)(ns < max_segments ? ns : max_segments);
+        scal[1] = ns <= max_segments ? s_t[1023] : 0;  // refuse to run an incomplete plan
+        scal[2] = s_p[1023];
+        scal[3] = 0;
+        scal[4] = 0;
+        scal[5] = 0;
+        scal[6] = ns > max_segments ? 1 : 0;
+    }
+}
+
+int plan_segments(const Bucketed &q, const Bucketed &d, const int32_t *d_group_k,
+                  const int32_t *d_group_metric, int tq, int tw, QueryPlan *plan, cudaStream_t st) {
+    k_plan_segments<<<1, 1024, 0, st>>>(q.b_start, q.b_count, q.nbins, d.b_start, d.b_count, d_group_k,
+                                        d_group_metric, tq, tw, plan->seg, plan->max_segments, plan->scal);
+    FP_LAUNCHED("k_plan_segments");
+    return FP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// distance functors
+// ---------------------------------------------------------------------------
+struct PosMasks {
+    uint32_t low, high, occ;
+};
+
+// F_D of one XOR word holding one 32-bit fingerprint.
+template <bool POS>
+__device__ __forceinline__ uint32_t fd32(uint32_t x, const PosMasks &M) {
+    if (!POS) return __popc(x);
+    // field is nonzero iff its top bit or a carry out of its low p-1 bits is set
+    uint32_t s = (x & M.low) + M.low;
+    return __popc(((s | x) & M.high) | (x & M.occ));
+}
+
+// F_D of the two 16-bit fingerprints packed in one XOR word (masks replicated
+// in both halves; per-field carries never cross a field, so never the halves).
+template <bool POS>
+__device__ __forceinline__ void fd16x2(uint32_t x, const PosMasks &M, uint32_t &lo, uint32_t &hi) {
+    uint32_t z = x;
+    if (POS) {
+        uint32_t s = (x & M.low) + M.low;
+        z = ((s | x) & M.high) | (x & M.occ);
+    }
+    lo = __popc(z & 0xFFFFu);
+    hi = __popc(z >> 16);
+}
+
+struct FilterArgs {
+    const uint32_t *qfp32;  // query fingerprints as 32-bit words (16-bit ones: one per u16 slot)
+    const uint16_t *qfp16;
+    const uint32_t *dfp;    // dictionary fingerprint words
+    const Segment *seg;
+    uint64_t *scal;         // [0] n_seg [1] tiles [3] tile counter [4] survivors
+    uint64_t *surv;
+    uint64_t surv_cap;
+    PosMasks M;
+    int tq;
+};
+
+__device__ __forceinline__ int find_segment(const Segment *seg, int nseg, uint64_t tile) {
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (seg[mid].tile_begin <= tile) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Thread layout of a tile.  Fingerprints arrive in 128-bit vectors of G
+// fingerprints (G = 4 for 32-bit, 8 for 16-bit); vector r of thread t holds
+// the tile's fingerprints r*(256*G) + t*G + (0..G-1), so one warp-wide load
+// reads 512 contiguous bytes.  Fingerprint i of a thread (0 <= i < NF) is at
+// tile offset (i/G)*(256*G) + t*G + i%G.
+template <int G>
+__device__ __forceinline__ uint32_t lane_offset(int i, int lane) {
+    return (uint32_t)(i / G) * (uint32_t)(FT_THREADS * G) + (uint32_t)lane * G + (uint32_t)(i % G);
+}
+
+// Appends the passing pairs of this warp for one query.  F[i] is the F_D of
+// the thread's fingerprint i; wbase is the slot of the warp's first
+// fingerprint, nvalid how many slots from wbase belong to the tile.
+template <int NF, int G>
+__device__ __forceinline__ void emit_survivors(const FilterArgs &A, uint32_t qslot, const uint32_t (&F)[NF],
+                                               uint32_t T, uint32_t wbase, uint32_t nvalid, int lane) {
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t total = 0;
+    unsigned bal[NF];
+#pragma unroll
+    for (int i = 0; i < NF; i++) {
+        bool pass = F[i] <= T && lane_offset<G>(i, lane) < nvalid;
+        bal[i] = __ballot_sync(0xffffffffu, pass);
+        total += __popc(bal[i]);
+    }
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd((unsigned long long *)&A.scal[4], (unsigned long long)total);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    uint32_t run = 0;
+#pragma unroll
+    for (int i = 0; i < NF; i++) {
+        if ((bal[i] >> lane) & 1u) {
+            uint64_t pos = base + run + __popc(bal[i] & lt);
+            if (pos < A.surv_cap)
+                A.surv[pos] = ((uint64_t)qslot << 32) | (uint64_t)(wbase + lane_offset<G>(i, lane));
+        }
+        run += __popc(bal[i]);
+    }
+}
+
+// W: fingerprint width; V: 32-bit words per thread (multiple of 4).
+template <int W, int V, bool POS>
+__global__ void __launch_bounds__(FT_THREADS) k_filter_tiled(FilterArgs A) {
+    constexpr int G = (W == 32) ? 4 : 8;             // fingerprints per 128-bit vector
+    constexpr int NF = (W == 32) ? V : 2 * V;        // fingerprints per thread
+    constexpr int TW = NF * FT_THREADS;              // fingerprints per tile
+    __shared__ uint32_t s_q[FT_MAX_TQ];
+    __shared__ uint64_t s_tile;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nseg = (int)A.scal[0];
+    const uint64_t ntiles = A.scal[1];
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd((unsigned long long *)&A.scal[3], 1ull);
+        __syncthreads();
+        const uint64_t tile = s_tile;
+        if (tile >= ntiles) break;
+        const Segment S = A.seg[find_segment(A.seg, nseg, tile)];
+        const uint64_t local = tile - S.tile_begin;
+        const uint32_t qt = (uint32_t)(local / S.n_dtiles), dt = (uint32_t)(local % S.n_dtiles);
+        const uint32_t q0 = S.q_start + qt * (uint32_t)A.tq;
+        const uint32_t nq = min((uint32_t)A.tq, S.q_count - qt * (uint32_t)A.tq);
+        const uint32_t w0 = S.d_start + dt * (uint32_t)TW;      // first fingerprint slot of the tile
+        const uint32_t nw = min((uint32_t)TW, S.d_count - dt * (uint32_t)TW);
+        const uint32_t T = 2u * (uint32_t)S.k;
+        for (uint32_t j = threadIdx.x; j < nq; j += FT_THREADS) {
+            uint32_t f = (W == 32) ? A.qfp32[q0 + j] : (uint32_t)A.qfp16[q0 + j];
+            s_q[j] = (W == 32) ? f : (f | (f << 16));
+        }
+        __syncthreads();
+        // the thread's dictionary fingerprints, as 32-bit words
+        uint32_t w[V];
+        const uint32_t word0 = (W == 32) ? w0 : w0 / 2;  // w0 is a multiple of 8 slots
+#pragma unroll
+        for (int r = 0; r < V / 4; r++) {
+            const uint4 x = *reinterpret_cast<const uint4 *>(A.dfp + word0 + r * (FT_THREADS * 4) + threadIdx.x * 4);
+            w[4 * r + 0] = x.x;
+            w[4 * r + 1] = x.y;
+            w[4 * r + 2] = x.z;
+            w[4 * r + 3] = x.w;
+        }
+        const uint32_t wbase = w0 + (uint32_t)warp * 32u * G;
+        const uint32_t wrel = (uint32_t)warp * 32u * G;
+        const uint32_t nvalid = nw > wrel ? nw - wrel : 0u;
+        const bool full = nw == (uint32_t)TW;
+        for (uint32_t j = 0; j < nq; j++) {
+            const uint32_t q = s_q[j];
+            uint32_t F[NF];
+            if (W == 32) {
+#pragma unroll
+                for (int v = 0; v < V; v++) F[v] = fd32<POS>(w[v] ^ q, A.M);
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; v++) fd16x2<POS>(w[v] ^ q, A.M, F[2 * v], F[2 * v + 1]);
+            }
+            if (!full) {
+#pragma unroll
+                for (int i = 0; i < NF; i++)
+                    if (lane_offset<G>(i, lane) >= nvalid) F[i] = 0xFFu;
+            }
+            uint32_t m = F[0];
+#pragma unroll
+            for (int i = 1; i < NF; i++) m = min(m, F[i]);
+            if (__any_sync(0xffffffffu, m <= T)) emit_survivors<NF, G>(A, q0 + j, F, T, wbase, nvalid, lane);
+        }
+        __syncthreads();
+    }
+}
+
+template <int W, int V, bool POS>
+static int launch_one(const FilterArgs &A, cudaStream_t st) {
+    static int grid = 0;
+    if (grid == 0) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_tiled<W, V, POS>, FT_THREADS, 0);
+        grid = sm_count() * (per_sm > 0 ? per_sm : 1);
+    }
+    k_filter_tiled<W, V, POS><<<grid, FT_THREADS, 0, st>>>(A);
+    FP_LAUNCHED("k_filter_tiled");
+    return FP_OK;
+}
+
+int tile_words(int width, int v) { return (width == 32 ? v : 2 * v) * FT_THREADS; }
+
+int launch_filter(const Bucketed &q, const Bucketed &d, const QueryPlan &plan, const FpParams &fp,
+                  const FilterCfg &cfg, uint64_t *surv, int64_t surv_cap, cudaStream_t st,
+                  int64_t *launches) {
+    FilterArgs A;
+    A.qfp32 = (const uint32_t *)q.fp;
+    A.qfp16 = (const uint16_t *)q.fp;
+    A.dfp = (const uint32_t *)d.fp;
+    A.seg = plan.seg;
+    A.scal = plan.scal;
+    A.surv = surv;
+    A.surv_cap = (uint64_t)surv_cap;
+    uint32_t rep = fp.width == 16 ? 16u : 0u;
+    A.M.low = fp.pos_low | (rep ? fp.pos_low << 16 : 0u);
+    A.M.high = fp.pos_high | (rep ? fp.pos_high << 16 : 0u);
+    A.M.occ = fp.pos_occ | (rep ? fp.pos_occ << 16 : 0u);
+    A.tq = cfg.tq < 1 ? 1 : (cfg.tq > FT_MAX_TQ ? FT_MAX_TQ : cfg.tq);
+    const bool pos = fp.type == FP_POS;
+    int rc;
+    if (fp.width == 32) {
+        if (cfg.v == 4) rc = pos ? launch_one<32, 4, true>(A, st) : launch_one<32, 4, false>(A, st);
+        else rc = pos ? launch_one<32, 8, true>(A, st) : launch_one<32, 8, false>(A, st);
+    } else {
+        if (cfg.v == 4) rc = pos ? launch_one<16, 4, true>(A, st) : launch_one<16, 4, false>(A, st);
+        else rc = pos ? launch_one<16, 8, true>(A, st) : launch_one<16, 8, false>(A, st);
+    }
+    if (launches) (*launches)++;
+    return rc;
+}
+
+}  // namespace fpk

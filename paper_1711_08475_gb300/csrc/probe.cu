@@ -1,0 +1,121 @@
+// Integer-pipe throughput probe (no counterpart in the paper: it measures the
+// GPU the filter runs on, to state the filter's arithmetic ceiling).
+//
+// kind 0 mirrors the filter's inner loop without its memory traffic: eight
+// register-resident dictionary fingerprints per thread, query fingerprints
+// read from shared memory, XOR + population count per pair, a minimum over
+// the eight, one compare with 2k.  kind 1 is independent chains of 3-input
+// logic operations, kind 2 independent chains of population counts.
+// Each block reads its SM cycle counter before and after the loop, so the
+// rate per SM per clock needs no knowledge of the clock.
+#include <vector>
+
+#include "common.cuh"
+
+namespace fpk {
+
+constexpr int PR_THREADS = 256;
+
+__global__ void __launch_bounds__(PR_THREADS) k_probe(int kind, int iters, uint32_t seed,
+                                                     unsigned long long *cycles, uint32_t *sink) {
+    __shared__ uint32_t s_q[64];
+    const uint32_t t = blockIdx.x * PR_THREADS + threadIdx.x;
+    if (threadIdx.x < 64) s_q[threadIdx.x] = (seed * 2654435761u) ^ (threadIdx.x * 0x9E3779B9u);
+    __syncthreads();
+    uint32_t w[8];
+#pragma unroll
+    for (int v = 0; v < 8; v++) w[v] = (t * 0x85EBCA6Bu) ^ (v * 0xC2B2AE35u) ^ seed;
+    uint32_t acc = 0;
+    const long long c0 = clock64();
+    if (kind == 0) {
+        for (int it = 0; it < iters; it++) {
+#pragma unroll 4
+            for (int j = 0; j < 64; j++) {
+                const uint32_t q = s_q[j];
+                uint32_t m = __popc(w[0] ^ q);
+#pragma unroll
+                for (int v = 1; v < 8; v++) m = min(m, (uint32_t)__popc(w[v] ^ q));
+                acc += m <= 2u;
+            }
+            w[it & 7] ^= acc;  // keeps the rounds from being folded together
+        }
+    } else if (kind == 1) {
+        uint32_t a[8];
+#pragma unroll
+        for (int v = 0; v < 8; v++) a[v] = w[v];
+        for (int it = 0; it < iters; it++) {
+#pragma unroll 8
+            for (int j = 0; j < 64; j++) {
+#pragma unroll
+                for (int v = 0; v < 8; v++) a[v] = (a[v] & w[(v + 1) & 7]) ^ w[(v + 3) & 7];  // one LOP3 each
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < 8; v++) acc ^= a[v];
+    } else {
+        uint32_t a[8];
+#pragma unroll
+        for (int v = 0; v < 8; v++) a[v] = w[v];
+        for (int it = 0; it < iters; it++) {
+#pragma unroll 8
+            for (int j = 0; j < 64; j++) {
+#pragma unroll
+                for (int v = 0; v < 8; v++) a[v] = __popc(a[v]);  // one POPC each
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < 8; v++) acc ^= a[v];
+    }
+    const long long c1 = clock64();
+    if (threadIdx.x == 0) cycles[blockIdx.x] = (unsigned long long)(c1 - c0);
+    if (acc == 0x12345678u) sink[t] = acc;
+}
+
+}  // namespace fpk
+
+using namespace fpk;
+
+extern "C" int fp_probe(int kind, int iters, void *cuda_stream, fp_probe_result *out) {
+    if (!out || kind < 0 || kind > 2 || iters <= 0) return FP_E_INVAL;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int per_sm = 0;
+    FP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe, PR_THREADS, 0));
+    if (per_sm < 1) per_sm = 1;
+    const int sms = sm_count();
+    const int grid = sms * per_sm;
+    unsigned long long *cyc = nullptr;
+    uint32_t *sink = nullptr;
+    FP_CUDA(cudaMalloc((void **)&cyc, sizeof(unsigned long long) * grid));
+    FP_CUDA(cudaMalloc((void **)&sink, sizeof(uint32_t) * grid * PR_THREADS));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    k_probe<<<grid, PR_THREADS, 0, st>>>(kind, iters / 8 + 1, 7u, cyc, sink);  // warm-up
+    g_launches++;
+    cudaEventRecord(e0, st);
+    k_probe<<<grid, PR_THREADS, 0, st>>>(kind, iters, 11u, cyc, sink);
+    g_launches++;
+    cudaEventRecord(e1, st);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    std::vector<unsigned long long> h(grid);
+    if (e == cudaSuccess) e = cudaMemcpy(h.data(), cyc, sizeof(unsigned long long) * grid, cudaMemcpyDeviceToHost);
+    cudaFree(cyc);
+    cudaFree(sink);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "fp_probe");
+    double mean_cyc = 0;
+    for (auto c : h) mean_cyc += (double)c;
+    mean_cyc /= grid;
+    const double per_thread = (double)iters * 64.0 * 8.0;  // pair tests, LOP3s or POPCs
+    out->kind = kind;
+    out->sm_count = sms;
+    out->ops = per_thread * PR_THREADS * grid;
+    out->seconds = ms * 1e-3;
+    out->ops_per_s = out->ops / out->seconds;
+    out->ops_per_clk_per_sm = per_thread * PR_THREADS * per_sm / mean_cyc;
+    out->sm_clock_mhz = mean_cyc / out->seconds * 1e-6;
+    return FP_OK;
+}

@@ -1,0 +1,213 @@
+// Explicit verification of the pairs the fingerprint bound could not reject
+// (Sec. 3: "when the fingerprint comparison is not decisive, we still have to
+// perform an explicit verification"; Sec. 4 for the two routines).
+//
+// Hamming (Sec. 4: compare characters until more than k mismatches): both
+// strings sit in zero-padded 16-byte rows of equal length, so the compare
+// runs over 128-bit words; a 32-bit word's mismatching bytes are counted with
+// the exact zero-byte test ((x & 0x7f..) + 0x7f.. | x) & 0x80.. on x = a ^ b,
+// and the loop stops as soon as the count exceeds k.
+//
+// Levenshtein (Sec. 4 uses the 2k+1 diagonal strip, Ukkonen 1985): cells
+// (i, j) with |i - j| > k cannot lie on an edit path of cost <= k, so only the
+// 2k+1 diagonals are kept, here as bits of a word.  The test is the anchored
+// Wu-Manber recurrence (Wu and Manber, "Fast text searching allowing errors",
+// CACM 1992) on that band: R_e holds the cells (i, j) of the current column
+// with D(i, j) <= e, bit b standing for row i = j - k + b.  Tying the bit to
+// the diagonal makes the diagonal move (match or substitution) shift-free,
+// the insertion move a right shift and the deletion move a left shift:
+//   R_0' = R_0 & Eq
+//   R_e' = (R_e & Eq) | R_{e-1} | (R_{e-1} >> 1) | (R_{e-1}' << 1)
+// Eq bit b says A[j-k+b-1] == B[j-1]; it is computed for all 2k+1 rows at once
+// with the zero-byte test on a byte window of A that slides one byte per
+// column.  Every move keeps or increases i, so bits for rows beyond |A| never
+// reach row |A| and need no mask.  Lev(A, B) <= k iff bit |A| - |B| + k of
+// R_k is set after the last column; the scan stops early once R_k is empty.
+#include "common.cuh"
+
+namespace fpk {
+
+struct VerifyArgs {
+    const uint64_t *surv;
+    const uint64_t *n_surv;
+    uint64_t surv_cap;
+    const uint8_t *q_len;
+    const uint32_t *q_row16;
+    const uint8_t *q_str;
+    const int32_t *q_idx;
+    const uint8_t *d_len;
+    const uint32_t *d_row16;
+    const uint8_t *d_str;
+    const int32_t *d_idx;
+    int idx_bits;
+    uint64_t *matches;
+    uint64_t *n_matches;
+    uint64_t match_cap;
+};
+
+// number of bytes of x that are zero
+__device__ __forceinline__ uint32_t zero_byte_mask(uint32_t x) {
+    return ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x | 0x7F7F7F7Fu);  // 0x80 in each zero byte
+}
+
+__device__ __forceinline__ bool ham_within(const uint8_t *a, const uint8_t *b, int len, int k) {
+    const uint4 *A = (const uint4 *)a, *B = (const uint4 *)b;
+    int mism = 0;
+    for (int c = 0; c < len; c += 16) {
+        uint4 x = A[c >> 4], y = B[c >> 4];
+        // mismatching bytes = 4 - zero bytes of the XOR (padding is zero on both sides)
+        mism += __popc(~zero_byte_mask(x.x ^ y.x) & 0x80808080u) + __popc(~zero_byte_mask(x.y ^ y.y) & 0x80808080u) +
+                __popc(~zero_byte_mask(x.z ^ y.z) & 0x80808080u) + __popc(~zero_byte_mask(x.w ^ y.w) & 0x80808080u);
+        if (mism > k) return false;
+    }
+    return true;
+}
+
+template <int K>
+__device__ __forceinline__ bool lev_within(const uint8_t *a, int m, const uint8_t *b, int n) {
+    constexpr int BAND = 2 * K + 1;
+    constexpr uint32_t BM = BAND >= 32 ? 0xFFFFFFFFu : ((1u << BAND) - 1u);
+    constexpr int PADW = (K + 3) / 4;  // zero words in front of A so that window offsets are >= 0
+    constexpr int NWIN = (BAND + 3) / 4;
+    constexpr int NREG = ((3 - K + 4 * PADW + 4 * (NWIN - 1)) >> 2) + 2;
+    const uint32_t *A32 = (const uint32_t *)a;
+    const uint32_t *B32 = (const uint32_t *)b;
+    uint32_t R[K + 1];
+#pragma unroll
+    for (int e = 0; e <= K; e++) R[e] = ((((e + 1) >= 32 ? 0xFFFFFFFFu : ((1u << (e + 1)) - 1u))) << K) & BM;
+    uint32_t w[NREG];
+#pragma unroll
+    for (int x = 0; x < NREG; x++) w[x] = x < PADW ? 0u : A32[x - PADW];
+    const int iters = (n + 3) >> 2;
+    for (int it = 0; it < iters; it++) {
+        const uint32_t bw = B32[it];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            if (4 * it + u < n) {
+                const uint32_t tt = ((bw >> (8 * u)) & 0xFFu) * 0x01010101u;
+                uint32_t eq = 0;
+#pragma unroll
+                for (int q = 0; q < NWIN; q++) {
+                    const int off = u - K + 4 * PADW + 4 * q;  // byte offset of the window word
+                    const int wi = off >> 2, sh = (off & 3) * 8;
+                    const uint32_t win = sh ? __funnelshift_r(w[wi], w[wi + 1], sh) : w[wi];
+                    const uint32_t z = zero_byte_mask(win ^ tt) >> 7;  // bits 0, 8, 16, 24
+                    eq |= ((z * 0x00204081u) >> 21 & 0xFu) << (4 * q);
+                }
+                eq &= BM;
+                uint32_t prev = R[0];
+                uint32_t cur = prev & eq;
+                R[0] = cur;
+#pragma unroll
+                for (int e = 1; e <= K; e++) {
+                    const uint32_t old = R[e];
+                    const uint32_t nv = ((old & eq) | prev | (prev >> 1) | (cur << 1)) & BM;
+                    prev = old;
+                    cur = nv;
+                    R[e] = nv;
+                }
+            }
+        }
+        if (R[K] == 0u) return false;
+#pragma unroll
+        for (int x = 0; x + 1 < NREG; x++) w[x] = w[x + 1];
+        const int nx = it + NREG - PADW;
+        w[NREG - 1] = nx < 0 ? 0u : A32[nx];
+    }
+    return (R[K] >> (m - n + K)) & 1u;
+}
+
+// metric 0: Hamming with runtime k; metric 1: Levenshtein with K.
+template <int METRIC, int K>
+__global__ void __launch_bounds__(256) k_verify(VerifyArgs A, int k) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t n0 = *A.n_surv;
+    const uint64_t n = n0 < A.surv_cap ? n0 : A.surv_cap;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const unsigned lt = (1u << lane) - 1u;
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n; base += stride) {
+        const uint64_t i = base + lane;
+        bool hit = false;
+        uint64_t key = 0;
+        if (i < n) {
+            const uint64_t s = A.surv[i];
+            const uint32_t qs = (uint32_t)(s >> 32), ds = (uint32_t)s;
+            const int m = A.q_len[qs], L = A.d_len[ds];
+            const uint8_t *qa = A.q_str + (uint64_t)A.q_row16[qs] * 16;
+            const uint8_t *da = A.d_str + (uint64_t)A.d_row16[ds] * 16;
+            if (METRIC == FP_HAM) hit = (m == L) && ham_within(qa, da, m, k);
+            else hit = (m - L <= K && L - m <= K) && lev_within<K>(qa, m, da, L);
+            if (hit) key = ((uint64_t)(uint32_t)A.q_idx[qs] << A.idx_bits) | (uint64_t)(uint32_t)A.d_idx[ds];
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, hit);
+        if (bal) {
+            unsigned long long mb = 0;
+            if (lane == 0) mb = atomicAdd((unsigned long long *)A.n_matches, (unsigned long long)__popc(bal));
+            mb = __shfl_sync(0xffffffffu, mb, 0);
+            if (hit) {
+                const uint64_t pos = mb + __popc(bal & lt);
+                if (pos < A.match_cap) A.matches[pos] = key;
+            }
+        }
+    }
+}
+
+template <int METRIC, int K>
+static int launch_verify_k(const VerifyArgs &A, int k, cudaStream_t st) {
+    static int grid = 0;
+    if (grid == 0) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_verify<METRIC, K>, 256, 0);
+        grid = sm_count() * (per_sm > 0 ? per_sm : 1);
+    }
+    k_verify<METRIC, K><<<grid, 256, 0, st>>>(A, k);
+    FP_LAUNCHED("k_verify");
+    return FP_OK;
+}
+
+int launch_verify_args(const VerifyArgs &A, int k, int metric, cudaStream_t st) {
+    if (metric == FP_HAM) return launch_verify_k<FP_HAM, 0>(A, k, st);
+    switch (k) {
+        case 0: return launch_verify_k<FP_LEV, 0>(A, k, st);
+        case 1: return launch_verify_k<FP_LEV, 1>(A, k, st);
+        case 2: return launch_verify_k<FP_LEV, 2>(A, k, st);
+        case 3: return launch_verify_k<FP_LEV, 3>(A, k, st);
+        case 4: return launch_verify_k<FP_LEV, 4>(A, k, st);
+        case 5: return launch_verify_k<FP_LEV, 5>(A, k, st);
+        case 6: return launch_verify_k<FP_LEV, 6>(A, k, st);
+        case 7: return launch_verify_k<FP_LEV, 7>(A, k, st);
+        case 8: return launch_verify_k<FP_LEV, 8>(A, k, st);
+        case 9: return launch_verify_k<FP_LEV, 9>(A, k, st);
+        case 10: return launch_verify_k<FP_LEV, 10>(A, k, st);
+        case 11: return launch_verify_k<FP_LEV, 11>(A, k, st);
+        case 12: return launch_verify_k<FP_LEV, 12>(A, k, st);
+        case 13: return launch_verify_k<FP_LEV, 13>(A, k, st);
+        case 14: return launch_verify_k<FP_LEV, 14>(A, k, st);
+        case 15: return launch_verify_k<FP_LEV, 15>(A, k, st);
+    }
+    return FP_E_INVAL;
+}
+
+int launch_verify(const Bucketed &q, const Bucketed &d, const uint64_t *surv, const uint64_t *d_n_surv,
+                  int64_t surv_cap, int k, int metric, int idx_bits, uint64_t *matches,
+                  uint64_t *d_n_matches, int64_t match_cap, cudaStream_t st) {
+    VerifyArgs A;
+    A.surv = surv;
+    A.n_surv = d_n_surv;
+    A.surv_cap = (uint64_t)surv_cap;
+    A.q_len = q.len;
+    A.q_row16 = q.row16;
+    A.q_str = q.str;
+    A.q_idx = q.idx;
+    A.d_len = d.len;
+    A.d_row16 = d.row16;
+    A.d_str = d.str;
+    A.d_idx = d.idx;
+    A.idx_bits = idx_bits;
+    A.matches = matches;
+    A.n_matches = d_n_matches;
+    A.match_cap = (uint64_t)match_cap;
+    return launch_verify_args(A, k, metric, st);
+}
+
+}  // namespace fpk
