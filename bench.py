@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--words", type=int, default=1_000_000)
     ap.add_argument("--queries", type=int, default=100_000)
     ap.add_argument("--fp-type", default="count")
-    ap.add_argument("--cpu-sample", type=int, default=240, help="queries in the CPU-oracle sample")
+    ap.add_argument("--cpu-sample", type=int, default=12000, help="queries in the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true", help="no CPU leg, no e2e, few steps (for ncu)")
     return ap.parse_args()

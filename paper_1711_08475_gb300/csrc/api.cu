@@ -509,12 +509,18 @@ int fp_query_ex(fp_index *ix, const uint8_t *chars, const int64_t *offsets, int6
             goto done;
         }
         if ((int64_t)scal[4] <= R.surv_cap && (int64_t)scal[5] <= R.match_cap) break;
-        // too small: redo filter, verify and emit with exact sizes
+        // too small: redo filter, verify and emit with exact sizes.  After a
+        // survivor overflow only part of the survivors were verified, so the
+        // match count is a lower bound and the survivor count bounds it.
         cudaFreeAsync(R.surv, st);
         cudaFreeAsync(R.matches, st);
         R.surv = R.matches = nullptr;
-        R.surv_cap = std::max<int64_t>(1, (int64_t)scal[4]);
-        R.match_cap = std::max<int64_t>(1, std::max<int64_t>((int64_t)scal[5], std::min<int64_t>(R.surv_cap, 1)));
+        if ((int64_t)scal[4] > R.surv_cap) {
+            R.surv_cap = std::max<int64_t>(1, (int64_t)scal[4]);
+            R.match_cap = R.surv_cap;
+        } else {
+            R.match_cap = std::max<int64_t>(1, (int64_t)scal[5]);
+        }
         if (attempt == 1) {
             rc = fail(FP_E_NOMEM, "survivor buffer sizing failed");
             goto done;

@@ -12,15 +12,23 @@
 // Per pair the work is one XOR and one population count (Sec. 3.3: F_D is
 // the Hamming weight of the XOR), or for position fingerprints a SWAR test of
 // which p-bit fields differ; the pair passes iff F_D <= 2k, i.e. iff
-// ceil(F_D / 2) <= k (Eq. 1).  A warp first asks whether any of its pairs
-// for the current query passed (min over its words, one vote); only then are
-// survivors compacted with ballots and appended to a global list.
+// ceil(F_D / 2) <= k (Eq. 1).
+//
+// Passing pairs are rare (well under 1% on the English-like workloads) but a
+// warp tests 256 pairs per query, so most warp-steps still hold one.  The hot
+// loop therefore only records, per thread, a bit per query saying "one of my
+// fingerprints passed" (min over its F_D values, one compare); after every 32
+// queries each thread re-tests just the queries whose bit is set and appends
+// the passing pairs to a per-warp buffer in shared memory.  A full buffer is
+// flushed to the global survivor list with one atomic reservation per flush.
 #include "common.cuh"
 
 namespace fpk {
 
 constexpr int FT_THREADS = 256;
+constexpr int FT_WARPS = FT_THREADS / 32;
 constexpr int FT_MAX_TQ = 256;
+constexpr int FT_STAGE = 256;  // staged survivors per warp
 
 // ---------------------------------------------------------------------------
 // tile planner: one block
@@ -121,7 +129,7 @@ struct PosMasks {
 template <bool POS>
 __device__ __forceinline__ uint32_t fd32(uint32_t x, const PosMasks &M) {
     if (!POS) return __popc(x);
-    // field is nonzero iff its top bit or a carry out of its low p-1 bits is set
+    // a field is nonzero iff its top bit or the carry out of its low p-1 bits is set
     uint32_t s = (x & M.low) + M.low;
     return __popc(((s | x) & M.high) | (x & M.occ));
 }
@@ -140,9 +148,9 @@ __device__ __forceinline__ void fd16x2(uint32_t x, const PosMasks &M, uint32_t &
 }
 
 struct FilterArgs {
-    const uint32_t *qfp32;  // query fingerprints as 32-bit words (16-bit ones: one per u16 slot)
-    const uint16_t *qfp16;
-    const uint32_t *dfp;    // dictionary fingerprint words
+    const uint32_t *qfp32;  // query fingerprints (32-bit slots)
+    const uint16_t *qfp16;  // query fingerprints (16-bit slots)
+    const uint32_t *dfp;    // dictionary fingerprints viewed as 32-bit words
     const Segment *seg;
     uint64_t *scal;         // [0] n_seg [1] tiles [3] tile counter [4] survivors
     uint64_t *surv;
@@ -165,53 +173,108 @@ __device__ __forceinline__ int find_segment(const Segment *seg, int nseg, uint64
 // fingerprints (G = 4 for 32-bit, 8 for 16-bit); vector r of thread t holds
 // the tile's fingerprints r*(256*G) + t*G + (0..G-1), so one warp-wide load
 // reads 512 contiguous bytes.  Fingerprint i of a thread (0 <= i < NF) is at
-// tile offset (i/G)*(256*G) + t*G + i%G.
+// tile offset (i/G)*(256*G) + t*G + i%G; relative to the warp's first slot it
+// is (i/G)*(256*G) + lane*G + i%G.
 template <int G>
 __device__ __forceinline__ uint32_t lane_offset(int i, int lane) {
     return (uint32_t)(i / G) * (uint32_t)(FT_THREADS * G) + (uint32_t)lane * G + (uint32_t)(i % G);
 }
 
-// Appends the passing pairs of this warp for one query.  F[i] is the F_D of
-// the thread's fingerprint i; wbase is the slot of the warp's first
-// fingerprint, nvalid how many slots from wbase belong to the tile.
-template <int NF, int G>
-__device__ __forceinline__ void emit_survivors(const FilterArgs &A, uint32_t qslot, const uint32_t (&F)[NF],
-                                               uint32_t T, uint32_t wbase, uint32_t nvalid, int lane) {
-    const unsigned lt = (1u << lane) - 1u;
-    uint32_t total = 0;
-    unsigned bal[NF];
+// All F_D values of a thread's fingerprints against query word q.
+template <int W, int V, bool POS, int NF>
+__device__ __forceinline__ void all_fd(const uint32_t (&w)[V], uint32_t q, const PosMasks &M, uint32_t (&F)[NF]) {
+    if (W == 32) {
 #pragma unroll
-    for (int i = 0; i < NF; i++) {
-        bool pass = F[i] <= T && lane_offset<G>(i, lane) < nvalid;
-        bal[i] = __ballot_sync(0xffffffffu, pass);
-        total += __popc(bal[i]);
+        for (int v = 0; v < V; v++) F[v] = fd32<POS>(w[v] ^ q, M);
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; v++) fd16x2<POS>(w[v] ^ q, M, F[2 * v], F[2 * v + 1]);
     }
+}
+
+// Moves the warp's staged survivors to the global list (one reservation).
+__device__ __forceinline__ void flush_stage(const FilterArgs &A, uint64_t *stage, uint32_t *cnt, int lane) {
+    __syncwarp();
+    const uint32_t c = min(*cnt, (uint32_t)FT_STAGE);
     unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd((unsigned long long *)&A.scal[4], (unsigned long long)total);
+    if (lane == 0 && c) base = atomicAdd((unsigned long long *)&A.scal[4], (unsigned long long)c);
     base = __shfl_sync(0xffffffffu, base, 0);
-    uint32_t run = 0;
+    for (uint32_t i = lane; i < c; i += 32) {
+        const uint64_t g = base + i;
+        if (g < A.surv_cap) A.surv[g] = stage[i];
+    }
+    __syncwarp();
+    if (lane == 0) *cnt = 0;
+    __syncwarp();
+}
+
+// One tile's pairs for the thread: queries s_q[0 .. nq) against its NF
+// fingerprints.  FULL = every fingerprint of the thread lies inside the tile.
+template <int W, int V, bool POS, bool FULL>
+__device__ __forceinline__ void scan_tile(const FilterArgs &A, const uint32_t *s_q, uint32_t nq, uint32_t q0,
+                                          const uint32_t (&w)[V], uint32_t invalid, uint32_t T, uint32_t wbase,
+                                          uint64_t *stage, uint32_t *cnt, int lane) {
+    constexpr int G = (W == 32) ? 4 : 8;
+    constexpr int NF = (W == 32) ? V : 2 * V;
+    for (uint32_t jb = 0; jb < nq; jb += 32) {
+        const uint32_t jn = min(32u, nq - jb);
+        uint32_t hits = 0;
+#pragma unroll 4
+        for (uint32_t jj = 0; jj < jn; jj++) {
+            uint32_t F[NF];
+            all_fd<W, V, POS, NF>(w, s_q[jb + jj], A.M, F);
+            if (!FULL) {
 #pragma unroll
-    for (int i = 0; i < NF; i++) {
-        if ((bal[i] >> lane) & 1u) {
-            uint64_t pos = base + run + __popc(bal[i] & lt);
-            if (pos < A.surv_cap)
-                A.surv[pos] = ((uint64_t)qslot << 32) | (uint64_t)(wbase + lane_offset<G>(i, lane));
+                for (int i = 0; i < NF; i++)
+                    if ((invalid >> i) & 1u) F[i] = 0xFFu;
+            }
+            uint32_t m = F[0];
+#pragma unroll
+            for (int i = 1; i < NF; i++) m = min(m, F[i]);
+            hits |= (m <= T ? 1u : 0u) << jj;
         }
-        run += __popc(bal[i]);
+        // re-test the queries that had a passing fingerprint in this thread
+        while (hits) {
+            const uint32_t jj = __ffs(hits) - 1;
+            hits &= hits - 1;
+            uint32_t F[NF];
+            all_fd<W, V, POS, NF>(w, s_q[jb + jj], A.M, F);
+#pragma unroll
+            for (int i = 0; i < NF; i++) {
+                if (F[i] <= T && (FULL || !((invalid >> i) & 1u))) {
+                    const uint64_t e = ((uint64_t)(q0 + jb + jj) << 32) | (uint64_t)(wbase + lane_offset<G>(i, lane));
+                    const uint32_t pos = atomicAdd(cnt, 1u);
+                    if (pos < FT_STAGE) {
+                        stage[pos] = e;
+                    } else {  // staging full: reserve a global slot directly
+                        const unsigned long long g = atomicAdd((unsigned long long *)&A.scal[4], 1ull);
+                        if (g < A.surv_cap) A.surv[g] = e;
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        if (*cnt >= FT_STAGE / 2) flush_stage(A, stage, cnt, lane);
     }
 }
 
 // W: fingerprint width; V: 32-bit words per thread (multiple of 4).
 template <int W, int V, bool POS>
-__global__ void __launch_bounds__(FT_THREADS) k_filter_tiled(FilterArgs A) {
+__global__ void __launch_bounds__(FT_THREADS, 4) k_filter_tiled(FilterArgs A) {
     constexpr int G = (W == 32) ? 4 : 8;             // fingerprints per 128-bit vector
     constexpr int NF = (W == 32) ? V : 2 * V;        // fingerprints per thread
     constexpr int TW = NF * FT_THREADS;              // fingerprints per tile
     __shared__ uint32_t s_q[FT_MAX_TQ];
+    __shared__ uint64_t s_stage[FT_WARPS][FT_STAGE];
+    __shared__ uint32_t s_cnt[FT_WARPS];
     __shared__ uint64_t s_tile;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nseg = (int)A.scal[0];
     const uint64_t ntiles = A.scal[1];
+    uint64_t *stage = s_stage[warp];
+    uint32_t *cnt = &s_cnt[warp];
+    if (lane == 0) *cnt = 0;
+    __syncwarp();
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd((unsigned long long *)&A.scal[3], 1ull);
         __syncthreads();
@@ -241,32 +304,21 @@ __global__ void __launch_bounds__(FT_THREADS) k_filter_tiled(FilterArgs A) {
             w[4 * r + 2] = x.z;
             w[4 * r + 3] = x.w;
         }
-        const uint32_t wbase = w0 + (uint32_t)warp * 32u * G;
         const uint32_t wrel = (uint32_t)warp * 32u * G;
+        const uint32_t wbase = w0 + wrel;
         const uint32_t nvalid = nw > wrel ? nw - wrel : 0u;
-        const bool full = nw == (uint32_t)TW;
-        for (uint32_t j = 0; j < nq; j++) {
-            const uint32_t q = s_q[j];
-            uint32_t F[NF];
-            if (W == 32) {
+        // fingerprints past the tile end must never pass
+        uint32_t invalid = 0;  // bit i: fingerprint i lies past the tile end
 #pragma unroll
-                for (int v = 0; v < V; v++) F[v] = fd32<POS>(w[v] ^ q, A.M);
-            } else {
-#pragma unroll
-                for (int v = 0; v < V; v++) fd16x2<POS>(w[v] ^ q, A.M, F[2 * v], F[2 * v + 1]);
-            }
-            if (!full) {
-#pragma unroll
-                for (int i = 0; i < NF; i++)
-                    if (lane_offset<G>(i, lane) >= nvalid) F[i] = 0xFFu;
-            }
-            uint32_t m = F[0];
-#pragma unroll
-            for (int i = 1; i < NF; i++) m = min(m, F[i]);
-            if (__any_sync(0xffffffffu, m <= T)) emit_survivors<NF, G>(A, q0 + j, F, T, wbase, nvalid, lane);
-        }
+        for (int i = 0; i < NF; i++)
+            if (lane_offset<G>(i, lane) >= nvalid) invalid |= 1u << i;
+        if (nw == (uint32_t)TW)
+            scan_tile<W, V, POS, true>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, lane);
+        else
+            scan_tile<W, V, POS, false>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, lane);
         __syncthreads();
     }
+    flush_stage(A, stage, cnt, lane);
 }
 
 template <int W, int V, bool POS>
@@ -295,7 +347,7 @@ int launch_filter(const Bucketed &q, const Bucketed &d, const QueryPlan &plan, c
     A.scal = plan.scal;
     A.surv = surv;
     A.surv_cap = (uint64_t)surv_cap;
-    uint32_t rep = fp.width == 16 ? 16u : 0u;
+    const bool rep = fp.width == 16;
     A.M.low = fp.pos_low | (rep ? fp.pos_low << 16 : 0u);
     A.M.high = fp.pos_high | (rep ? fp.pos_high << 16 : 0u);
     A.M.occ = fp.pos_occ | (rep ? fp.pos_occ << 16 : 0u);

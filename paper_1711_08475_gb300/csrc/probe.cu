@@ -46,8 +46,13 @@ __global__ void __launch_bounds__(PR_THREADS) k_probe(int kind, int iters, uint3
         for (int it = 0; it < iters; it++) {
 #pragma unroll 8
             for (int j = 0; j < 64; j++) {
+                // eight independent 3-input logic operations per step, each reading
+                // the previous step's values of other chains (nothing to fold)
+                uint32_t b[8];
 #pragma unroll
-                for (int v = 0; v < 8; v++) a[v] = (a[v] & w[(v + 1) & 7]) ^ w[(v + 3) & 7];  // one LOP3 each
+                for (int v = 0; v < 8; v++) b[v] = (a[v] & a[(v + 1) & 7]) ^ a[(v + 3) & 7];
+#pragma unroll
+                for (int v = 0; v < 8; v++) a[v] = b[v];
             }
         }
 #pragma unroll
