@@ -175,7 +175,7 @@ def fp_build(chars, offsets=None, fp_type: str = "occ", width: int = 32, symbol_
 
 
 def fp_query_ex(index: Index, chars, offsets=None, k: int = 1, metric: str = "ham", mode: str = "tiled",
-                tile_queries: int = 0, words_per_thread: int = 0, stream=None) -> Result:
+                tile_queries: int = 0, words_per_thread: int = 0, variant: int = 0, stream=None) -> Result:
     """Match lists of a pattern batch (fp_query_ex in include/fp.h)."""
     L = load()
     chars, offsets, n = _strings(chars, offsets)
@@ -183,6 +183,7 @@ def fp_query_ex(index: Index, chars, offsets=None, k: int = 1, metric: str = "ha
     o.mode = MODES[mode]
     o.tile_queries = tile_queries
     o.words_per_thread = words_per_thread
+    o.variant = variant
     cp, k1 = _ptr(chars)
     op, k2 = _ptr(offsets)
     h = ctypes.c_void_p()

@@ -390,8 +390,11 @@ int fp_query_ex(fp_index *ix, const uint8_t *chars, const int64_t *offsets, int6
     if (o.mode != FP_MODE_TILED && o.mode != FP_MODE_PLAIN) return fail(FP_E_UNSUPPORTED, "query mode not available");
     FilterCfg cfg;
     cfg.mode = o.mode;
-    cfg.v = o.words_per_thread == 4 ? 4 : 8;
-    cfg.tq = o.mode == FP_MODE_PLAIN ? 1 : (o.tile_queries > 0 ? std::min(o.tile_queries, 256) : 64);
+    // defaults from a sweep on the 1M-word English-like workload: 4 words per
+    // thread, 256 queries per tile
+    cfg.v = o.words_per_thread == 8 ? 8 : 4;
+    cfg.tq = o.mode == FP_MODE_PLAIN ? 1 : (o.tile_queries > 0 ? std::min(o.tile_queries, 256) : 256);
+    cfg.k1mix = o.variant == 0 && k == 1;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     init_pool();
 

@@ -128,6 +128,7 @@ struct FilterCfg {
     int mode;      // fp_mode
     int tq;        // queries per tile
     int v;         // 32-bit fingerprint words per thread (4 or 8)
+    bool k1mix;    // k = 1: test a quarter of the words with integer ALU ops instead of POPC
 };
 
 int plan_segments(const Bucketed &q, const Bucketed &d, const int32_t *d_group_k,

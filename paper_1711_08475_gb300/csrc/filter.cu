@@ -208,35 +208,103 @@ __device__ __forceinline__ void flush_stage(const FilterArgs &A, uint64_t *stage
     __syncwarp();
 }
 
+// x has at most two bits set: clear the lowest set bit twice (integer ALU
+// only, no population count).  Used for k = 1 on part of a thread's words so
+// that the population-count pipe and the logic pipe share the work.
+__device__ __forceinline__ uint32_t clear2(uint32_t x) {
+    const uint32_t t = x & (x - 1u);
+    return t & (t - 1u);  // zero iff popc(x) <= 2
+}
+
+// Minimum of n values with 3-input minima.
+template <int N>
+__device__ __forceinline__ uint32_t min_tree(const uint32_t *v) {
+    if (N == 1) return v[0];
+    if (N == 2) return min(v[0], v[1]);
+    if (N == 3) return __vimin3_u32(v[0], v[1], v[2]);
+    return __vimin3_u32(min_tree<N / 3>(v), min_tree<N / 3>(v + N / 3), min_tree<N - 2 * (N / 3)>(v + 2 * (N / 3)));
+}
+
+// A value whose sign bit says "some fingerprint of the thread passes against
+// query word q" (min over F_D - (2k+1) < 0).  It may also be negative when
+// nothing passes (only with K1MIX, for words of 0xFFFFFFFE or more after the
+// two clears): a spurious hit only costs an exact re-test, a missed pass cannot
+// happen.  K1MIX (32-bit occ/occh/count, k = 1): the last quarter of the words
+// is tested with clear2 instead of the population count (passes iff clear2 == 0,
+// i.e. iff clear2 + 2 <= 2, so it joins the same minimum).
+template <int W, int V, bool POS, bool FULL, bool K1MIX>
+__device__ __forceinline__ int32_t pass_sign(const uint32_t (&w)[V], uint32_t q, const PosMasks &M,
+                                             uint32_t invalid, uint32_t T) {
+    if (K1MIX) {
+        constexpr int NZ = V / 4, NP = V - NZ;  // NP words through POPC, NZ through clear2
+        uint32_t f[NP + 1];
+#pragma unroll
+        for (int v = 0; v < NP; v++) {
+            f[v] = __popc(w[v] ^ q);
+            if (!FULL && ((invalid >> v) & 1u)) f[v] = 0xFFu;
+        }
+        uint32_t z[NZ];
+#pragma unroll
+        for (int v = 0; v < NZ; v++) {
+            z[v] = clear2(w[NP + v] ^ q);
+            if (!FULL && ((invalid >> (NP + v)) & 1u)) z[v] = 1u;
+        }
+        f[NP] = min_tree<NZ>(z) + 2u;
+        return (int32_t)(min_tree<NP + 1>(f) - 3u);
+    } else {
+        constexpr int NF = (W == 32) ? V : 2 * V;
+        uint32_t f[NF];
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            if (W == 32) {
+                f[v] = fd32<POS>(w[v] ^ q, M);
+            } else {
+                fd16x2<POS>(w[v] ^ q, M, f[2 * v], f[2 * v + 1]);
+            }
+        }
+        if (!FULL) {
+#pragma unroll
+            for (int i = 0; i < NF; i++)
+                if ((invalid >> i) & 1u) f[i] = 0xFFu;
+        }
+        return (int32_t)(min_tree<NF>(f) - (T + 1u));
+    }
+}
+
 // One tile's pairs for the thread: queries s_q[0 .. nq) against its NF
 // fingerprints.  FULL = every fingerprint of the thread lies inside the tile.
-template <int W, int V, bool POS, bool FULL>
+// Query fingerprints are read four at a time (one 128-bit shared load), the
+// four tests are independent, and each test's sign bit is shifted into the
+// hit mask (bit b of a 32-query batch <-> query jn4 - 1 - b).
+template <int W, int V, bool POS, bool FULL, bool K1MIX>
 __device__ __forceinline__ void scan_tile(const FilterArgs &A, const uint32_t *s_q, uint32_t nq, uint32_t q0,
                                           const uint32_t (&w)[V], uint32_t invalid, uint32_t T, uint32_t wbase,
                                           uint64_t *stage, uint32_t *cnt, int lane) {
     constexpr int G = (W == 32) ? 4 : 8;
     constexpr int NF = (W == 32) ? V : 2 * V;
+    const uint4 *s_q4 = reinterpret_cast<const uint4 *>(s_q);
     for (uint32_t jb = 0; jb < nq; jb += 32) {
         const uint32_t jn = min(32u, nq - jb);
+        const uint32_t jn4 = (jn + 3u) & ~3u;
         uint32_t hits = 0;
-#pragma unroll 4
-        for (uint32_t jj = 0; jj < jn; jj++) {
-            uint32_t F[NF];
-            all_fd<W, V, POS, NF>(w, s_q[jb + jj], A.M, F);
-            if (!FULL) {
-#pragma unroll
-                for (int i = 0; i < NF; i++)
-                    if ((invalid >> i) & 1u) F[i] = 0xFFu;
-            }
-            uint32_t m = F[0];
-#pragma unroll
-            for (int i = 1; i < NF; i++) m = min(m, F[i]);
-            hits |= (m <= T ? 1u : 0u) << jj;
+#pragma unroll 2
+        for (uint32_t jj = 0; jj < jn; jj += 4) {
+            const uint4 q4 = s_q4[(jb + jj) >> 2];
+            const int32_t h0 = pass_sign<W, V, POS, FULL, K1MIX>(w, q4.x, A.M, invalid, T);
+            const int32_t h1 = pass_sign<W, V, POS, FULL, K1MIX>(w, q4.y, A.M, invalid, T);
+            const int32_t h2 = pass_sign<W, V, POS, FULL, K1MIX>(w, q4.z, A.M, invalid, T);
+            const int32_t h3 = pass_sign<W, V, POS, FULL, K1MIX>(w, q4.w, A.M, invalid, T);
+            hits = __funnelshift_l((uint32_t)h0, hits, 1);
+            hits = __funnelshift_l((uint32_t)h1, hits, 1);
+            hits = __funnelshift_l((uint32_t)h2, hits, 1);
+            hits = __funnelshift_l((uint32_t)h3, hits, 1);
         }
-        // re-test the queries that had a passing fingerprint in this thread
+        hits &= ~((1u << (jn4 - jn)) - 1u);  // queries past nq in the last group of four
+        // re-test, exactly, the queries that had a (possible) passing fingerprint
         while (hits) {
-            const uint32_t jj = __ffs(hits) - 1;
+            const uint32_t b = __ffs(hits) - 1;
             hits &= hits - 1;
+            const uint32_t jj = jn4 - 1u - b;
             uint32_t F[NF];
             all_fd<W, V, POS, NF>(w, s_q[jb + jj], A.M, F);
 #pragma unroll
@@ -259,12 +327,12 @@ __device__ __forceinline__ void scan_tile(const FilterArgs &A, const uint32_t *s
 }
 
 // W: fingerprint width; V: 32-bit words per thread (multiple of 4).
-template <int W, int V, bool POS>
-__global__ void __launch_bounds__(FT_THREADS, 4) k_filter_tiled(FilterArgs A) {
+template <int W, int V, bool POS, bool K1MIX>
+__global__ void __launch_bounds__(FT_THREADS, 5) k_filter_tiled(FilterArgs A) {
     constexpr int G = (W == 32) ? 4 : 8;             // fingerprints per 128-bit vector
     constexpr int NF = (W == 32) ? V : 2 * V;        // fingerprints per thread
     constexpr int TW = NF * FT_THREADS;              // fingerprints per tile
-    __shared__ uint32_t s_q[FT_MAX_TQ];
+    __shared__ __align__(16) uint32_t s_q[FT_MAX_TQ];
     __shared__ uint64_t s_stage[FT_WARPS][FT_STAGE];
     __shared__ uint32_t s_cnt[FT_WARPS];
     __shared__ uint64_t s_tile;
@@ -312,24 +380,36 @@ __global__ void __launch_bounds__(FT_THREADS, 4) k_filter_tiled(FilterArgs A) {
 #pragma unroll
         for (int i = 0; i < NF; i++)
             if (lane_offset<G>(i, lane) >= nvalid) invalid |= 1u << i;
-        if (nw == (uint32_t)TW)
-            scan_tile<W, V, POS, true>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, lane);
-        else
-            scan_tile<W, V, POS, false>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, lane);
+        if (K1MIX && T != 2u) {  // a k = 1 variant given another k: exact general path
+            if (nw == (uint32_t)TW)
+                scan_tile<W, V, POS, true, false>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, lane);
+            else
+                scan_tile<W, V, POS, false, false>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, lane);
+        } else if (nw == (uint32_t)TW) {
+            scan_tile<W, V, POS, true, K1MIX>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, lane);
+        } else {
+            scan_tile<W, V, POS, false, K1MIX>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, lane);
+        }
         __syncthreads();
     }
     flush_stage(A, stage, cnt, lane);
 }
 
 template <int W, int V, bool POS>
-static int launch_one(const FilterArgs &A, cudaStream_t st) {
-    static int grid = 0;
-    if (grid == 0) {
+static int launch_one(const FilterArgs &A, bool k1mix, cudaStream_t st) {
+    static int grid[2] = {0, 0};
+    int &g = grid[k1mix ? 1 : 0];
+    if (g == 0) {
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_tiled<W, V, POS>, FT_THREADS, 0);
-        grid = sm_count() * (per_sm > 0 ? per_sm : 1);
+        if (k1mix)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_tiled<W, V, POS, (W == 32 && !POS)>,
+                                                          FT_THREADS, 0);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_tiled<W, V, POS, false>, FT_THREADS, 0);
+        g = sm_count() * (per_sm > 0 ? per_sm : 1);
     }
-    k_filter_tiled<W, V, POS><<<grid, FT_THREADS, 0, st>>>(A);
+    if (k1mix) k_filter_tiled<W, V, POS, (W == 32 && !POS)><<<g, FT_THREADS, 0, st>>>(A);
+    else k_filter_tiled<W, V, POS, false><<<g, FT_THREADS, 0, st>>>(A);
     FP_LAUNCHED("k_filter_tiled");
     return FP_OK;
 }
@@ -353,13 +433,15 @@ int launch_filter(const Bucketed &q, const Bucketed &d, const QueryPlan &plan, c
     A.M.occ = fp.pos_occ | (rep ? fp.pos_occ << 16 : 0u);
     A.tq = cfg.tq < 1 ? 1 : (cfg.tq > FT_MAX_TQ ? FT_MAX_TQ : cfg.tq);
     const bool pos = fp.type == FP_POS;
+    // the mixed POPC / ALU test applies to 32-bit popcount-type fingerprints at k = 1
+    const bool mix = cfg.k1mix && fp.width == 32 && !pos;
     int rc;
     if (fp.width == 32) {
-        if (cfg.v == 4) rc = pos ? launch_one<32, 4, true>(A, st) : launch_one<32, 4, false>(A, st);
-        else rc = pos ? launch_one<32, 8, true>(A, st) : launch_one<32, 8, false>(A, st);
+        if (cfg.v == 4) rc = pos ? launch_one<32, 4, true>(A, false, st) : launch_one<32, 4, false>(A, mix, st);
+        else rc = pos ? launch_one<32, 8, true>(A, false, st) : launch_one<32, 8, false>(A, mix, st);
     } else {
-        if (cfg.v == 4) rc = pos ? launch_one<16, 4, true>(A, st) : launch_one<16, 4, false>(A, st);
-        else rc = pos ? launch_one<16, 8, true>(A, st) : launch_one<16, 8, false>(A, st);
+        if (cfg.v == 4) rc = pos ? launch_one<16, 4, true>(A, false, st) : launch_one<16, 4, false>(A, false, st);
+        else rc = pos ? launch_one<16, 8, true>(A, false, st) : launch_one<16, 8, false>(A, false, st);
     }
     if (launches) (*launches)++;
     return rc;

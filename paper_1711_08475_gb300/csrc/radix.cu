@@ -42,27 +42,42 @@ __global__ void __launch_bounds__(RB_THREADS) k_radix_hist(const uint64_t *__res
     hist[(size_t)threadIdx.x * nb + b] = h[threadIdx.x];
 }
 
-// Exclusive scan of n uint32 values in place, one block of 1024 threads.
+// Exclusive scan of n uint32 values in place, one block of 1024 threads that
+// walks the array in coalesced rounds of 1024 (warp shuffles inside a warp,
+// one shared step across the 32 warps, a carry between rounds).
 __global__ void __launch_bounds__(1024) k_scan_u32(uint32_t *__restrict__ a, int64_t n) {
-    __shared__ uint32_t part[1024];
-    const int t = threadIdx.x;
-    int64_t per = (n + 1023) / 1024;
-    int64_t lo = per * t, hi = lo + per < n ? lo + per : n;
-    uint32_t s = 0;
-    for (int64_t i = lo; i < hi; i++) s += a[i];
-    part[t] = s;
+    __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_carry;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    if (t == 0) s_carry = 0;
     __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        uint32_t v = t >= off ? part[t - off] : 0;
+    for (int64_t base = 0; base < n; base += 1024) {
+        const int64_t i = base + t;
+        const uint32_t v = i < n ? a[i] : 0u;
+        uint32_t x = v;  // inclusive scan within the warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[w] = x;
         __syncthreads();
-        part[t] += v;
+        if (w == 0) {
+            uint32_t s = s_warp[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += y;
+            }
+            s_warp[lane] = s;  // inclusive over warps
+        }
         __syncthreads();
-    }
-    uint32_t run = part[t] - s;
-    for (int64_t i = lo; i < hi; i++) {
-        uint32_t v = a[i];
-        a[i] = run;
-        run += v;
+        const uint32_t carry = s_carry;
+        const uint32_t before = (w ? s_warp[w - 1] : 0u) + x - v;
+        if (i < n) a[i] = carry + before;
+        __syncthreads();
+        if (t == 1023) s_carry = carry + s_warp[31];
+        __syncthreads();
     }
 }
 
@@ -137,7 +152,7 @@ int radix_sort_u64(uint64_t *keys, uint64_t *tmp, const uint64_t *d_n, int64_t m
     *result = keys;
     if (max_n <= 0 || bits_hi <= bits_lo) return FP_OK;
     int64_t nb64 = (max_n + 4095) / 4096;
-    int nb = (int)(nb64 < 1 ? 1 : (nb64 > 1024 ? 1024 : nb64));
+    int nb = (int)(nb64 < 1 ? 1 : (nb64 > 256 ? 256 : nb64));
     uint32_t *hist = nullptr;
     FP_CUDA(cudaMallocAsync((void **)&hist, sizeof(uint32_t) * 256 * (size_t)nb, st));
     uint64_t *src = keys, *dst = tmp;

@@ -26,7 +26,7 @@ class fp_build_opts(ctypes.Structure):
 
 class fp_query_opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("tile_queries", ctypes.c_int32),
-                ("words_per_thread", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("words_per_thread", ctypes.c_int32), ("variant", ctypes.c_int32)]
 
 
 class fp_stats(ctypes.Structure):
