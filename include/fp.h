@@ -151,6 +151,44 @@ FP_API int fp_query(fp_index *ix, const uint8_t *chars, const int64_t *offsets, 
 FP_API int fp_query_ex(fp_index *ix, const uint8_t *chars, const int64_t *offsets, int64_t n_queries, int k,
                 int metric, const fp_query_opts *opts, void *cuda_stream, fp_result **out);
 
+/* ---- query without device allocation ------------------------------------ */
+/* The paper has no counterpart to this entry point: it is a deployment aid.
+ * Same result as fp_query for small batches, but the call allocates no device
+ * memory at all (no cudaMalloc, no stream-ordered pool, no library that
+ * allocates): all of its working memory is one fixed scratch array of
+ * FP_NOALLOC_SCRATCH_BYTES compiled into the library, which every GPU that
+ * loads the library holds until the process exits.  It is meant for callers
+ * that cannot allocate once they are serving -- e.g. a process whose device
+ * memory is carved up in advance by its own allocator, or a latency-critical
+ * loop that must not risk the device-wide synchronisation an allocation can
+ * cause.
+ *   chars, offsets: DEVICE memory, offsets[0] == 0, n_queries + 1 entries.
+ *   n_queries <= FP_NOALLOC_MAX_QUERIES, offsets[n] <= FP_NOALLOC_MAX_CHARS.
+ *   row_ptr: DEVICE, n_queries + 1 int64 (written); idx: DEVICE, idx_capacity
+ *   int32 (written, ascending per query as in fp_query).
+ *   n_matches: host; set to the number of matches (also when it exceeds the
+ *   capacity, so the caller can retry with a larger idx buffer).
+ * Errors: FP_E_INVAL (sizes beyond the limits, host pointers, bad offsets),
+ * FP_E_UNSUPPORTED (as fp_query), FP_E_OVERFLOW (more than
+ * FP_NOALLOC_MAX_CANDIDATES pairs passed the filter, or more matches than
+ * min(idx_capacity, FP_NOALLOC_MAX_MATCHES); outputs are then not valid),
+ * FP_E_CUDA.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array and it keeps the
+ * last call's contents (each call clears what must start at zero).  Calls
+ * whose GPU work overlapped would race, so calls are serialised by a
+ * process-wide lock and each call synchronises cuda_stream before it
+ * returns. */
+#define FP_NOALLOC_MAX_QUERIES 4096
+#define FP_NOALLOC_MAX_CHARS 262144
+#define FP_NOALLOC_MAX_CANDIDATES 1048576
+#define FP_NOALLOC_MAX_MATCHES 262144
+#define FP_NOALLOC_SCRATCH_BYTES (14 * 1024 * 1024)
+FP_API int fp_query_noalloc(fp_index *ix, const uint8_t *chars, const int64_t *offsets, int64_t n_queries, int k,
+                            int metric, int64_t *row_ptr, int32_t *idx, int64_t idx_capacity, int64_t *n_matches,
+                            void *cuda_stream);
+
 /* ---- results ------------------------------------------------------------ */
 /* CSR of match lists: row_ptr[n_queries + 1] (int64) and idx[row_ptr[n]]
  * (int32, strictly ascending within a row; duplicate dictionary strings are

@@ -144,19 +144,6 @@ static int stage_strings(const uint8_t *chars, const int64_t *off, int64_t n, cu
 
 using namespace fpk;
 
-struct fp_index {
-    FpParams P{};
-    int set = 0;
-    int64_t n_words = 0;
-    Bucketed D;
-    int8_t *d_map = nullptr;
-    int8_t h_map[256];
-    unsigned long long *d_counts = nullptr;
-    int32_t h_count[256];
-    int32_t h_start[256];
-    int idx_bits = 1;
-    int64_t device_bytes = 0;
-};
 
 struct fp_result {
     int64_t n_queries = 0;
@@ -462,7 +449,10 @@ int fp_query_ex(fp_index *ix, const uint8_t *chars, const int64_t *offsets, int6
         }
         pairs_bound = widest * n_queries;
     }
-    R.surv_cap = std::max<int64_t>(1, std::min<int64_t>(pairs_bound, std::max<int64_t>(1 << 20, pairs_bound / 16)));
+    // survivors are sized from the pass ratio seen on this index before (x1.5),
+    // 1/64 of the pairs at first; a larger count reruns the pass with exact sizes
+    R.surv_cap = std::max<int64_t>(
+        1, std::min<int64_t>(pairs_bound, std::max<int64_t>(1 << 20, (int64_t)(pairs_bound * ix->surv_ratio * 1.5))));
     R.match_cap = std::max<int64_t>(1, std::min<int64_t>(R.surv_cap, std::max<int64_t>(1 << 20, n_queries * 64)));
     CK(cudaEventRecord(R.ev[1], st));
     for (int attempt = 0; attempt < 2; attempt++) {
@@ -532,6 +522,7 @@ int fp_query_ex(fp_index *ix, const uint8_t *chars, const int64_t *offsets, int6
     res->n_matches = (int64_t)scal[5];
     res->stats.pairs = (int64_t)scal[2];
     res->stats.survivors = (int64_t)scal[4];
+    if (scal[2] > 0) ix->surv_ratio = std::max(1.0 / 4096.0, (double)scal[4] / (double)scal[2]);
     res->stats.matches = (int64_t)scal[5];
     cudaEventElapsedTime(&res->stats.ms_prepare, R.ev[0], R.ev[1]);
     cudaEventElapsedTime(&res->stats.ms_filter, R.ev[1], R.ev[2]);

@@ -501,3 +501,58 @@ int refingerprint(Bucketed *B, const int8_t *d_map, const FpParams &P, cudaStrea
 }
 
 }  // namespace fpk
+
+namespace fpk {
+
+// bucketize() into arrays the caller has placed in B (fp, idx, len, row16,
+// str, b_start, b_count, sized for n strings of total_chars bytes and 256
+// length bins) with the temporaries in S; allocates nothing.  One group only.
+int bucketize_into(const uint8_t *d_chars, const int64_t *d_off, int64_t n, int64_t total_chars,
+                   const int8_t *d_map, const FpParams &P, cudaStream_t st, Bucketed *B, const BucketScratch &S,
+                   int32_t *d_err) {
+    const int nbins = 256;
+    const int64_t slots_ub = n + (int64_t)(SLOT_ALIGN - 1) * nbins;
+    const int64_t str_ub = total_chars + 15 * n;
+    const size_t fpw = P.width == 16 ? 2 : 4;
+    B->nbins = nbins;
+    B->n = n;
+    B->stream_ordered = false;
+    FP_CUDA(cudaMemsetAsync(B->fp, 0, (slots_ub + FP_SLACK_SLOTS) * fpw, st));
+    FP_CUDA(cudaMemsetAsync(B->idx, 0xFF, slots_ub * 4, st));
+    FP_CUDA(cudaMemsetAsync(B->len, 0, slots_ub, st));
+    FP_CUDA(cudaMemsetAsync(B->row16, 0, slots_ub * 4, st));
+    FP_CUDA(cudaMemsetAsync(B->str + str_ub, 0, STR_SLACK, st));
+    FP_CUDA(cudaMemsetAsync(S.hist, 0, nbins * 4, st));
+    if (n > 0) {
+        int g = grid_for(n, 256, 2048);
+        k_bin_keys<<<g, 256, nbins * sizeof(int32_t), st>>>(d_off, n, nullptr, nbins, S.keys, S.hist, d_err);
+        FP_LAUNCHED("k_bin_keys");
+    }
+    k_plan_bins<<<1, 1024, 0, st>>>(S.hist, nbins, B->b_start, B->b_count, S.ustart, S.str16, S.tot);
+    FP_LAUNCHED("k_plan_bins");
+    if (n > 0) {
+        uint64_t *sorted = S.keys;
+        FP_TRY(radix_sort_u64_into(S.keys, S.keys2, S.radix_hist, nullptr, n, 32, 40, st, &sorted));
+        int g = grid_for(n, 256, 8192);
+        switch (P.type) {
+            case FP_OCC:
+                k_scatter_fp<FP_OCC><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B->b_start, S.ustart, S.str16, *B);
+                break;
+            case FP_OCC_HALVED:
+                k_scatter_fp<FP_OCC_HALVED><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B->b_start, S.ustart, S.str16, *B);
+                break;
+            case FP_COUNT:
+                k_scatter_fp<FP_COUNT><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B->b_start, S.ustart, S.str16, *B);
+                break;
+            default:
+                k_scatter_fp<FP_POS><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B->b_start, S.ustart, S.str16, *B);
+                break;
+        }
+        FP_LAUNCHED("k_scatter_fp");
+    }
+    B->n_slots = slots_ub;
+    B->str_bytes = str_ub;
+    return FP_OK;
+}
+
+}  // namespace fpk

@@ -150,4 +150,39 @@ int build_csr(uint64_t *keys, uint64_t *tmp, const uint64_t *d_n, int64_t max_n,
 
 int sm_count();
 
+// ---------------------------------------------------------------------------
+// the same steps on caller-placed buffers (nothing is allocated)
+// ---------------------------------------------------------------------------
+struct BucketScratch {
+    uint64_t *keys, *keys2;  // n keys each
+    int32_t *hist, *ustart;  // 256 each
+    int64_t *str16;          // 256
+    int64_t *tot;            // 2
+    uint32_t *radix_hist;    // 256 * radix_blocks(n)
+};
+int radix_blocks(int64_t max_n);
+int radix_sort_u64_into(uint64_t *keys, uint64_t *tmp, uint32_t *hist, const uint64_t *d_n, int64_t max_n,
+                        int bits_lo, int bits_hi, cudaStream_t st, uint64_t **result);
+int build_csr_into(uint64_t *keys, uint64_t *tmp, uint32_t *hist, const uint64_t *d_n, int64_t max_n, int q_bits,
+                   int idx_bits, int64_t n_queries, int64_t *row_ptr, int32_t *idx, cudaStream_t st);
+int bucketize_into(const uint8_t *d_chars, const int64_t *d_off, int64_t n, int64_t total_chars,
+                   const int8_t *d_map, const FpParams &P, cudaStream_t st, Bucketed *B, const BucketScratch &S,
+                   int32_t *d_err);
+
 }  // namespace fpk
+
+// The resident dictionary behind the opaque fp_index handle.
+struct fp_index {
+    fpk::FpParams P{};
+    int set = 0;
+    int64_t n_words = 0;
+    fpk::Bucketed D;
+    int8_t *d_map = nullptr;
+    int8_t h_map[256];
+    unsigned long long *d_counts = nullptr;
+    int32_t h_count[256];
+    int32_t h_start[256];
+    int idx_bits = 1;
+    int64_t device_bytes = 0;
+    double surv_ratio = 1.0 / 64.0;  // survivors / pairs of the last query (sizes the next survivor buffer)
+};

@@ -193,3 +193,58 @@ int build_csr(uint64_t *keys, uint64_t *tmp, const uint64_t *d_n, int64_t max_n,
 }
 
 }  // namespace fpk
+
+namespace fpk {
+
+// Blocks per radix pass for a capacity of max_n keys (the digit histogram
+// holds 256 entries per block).
+int radix_blocks(int64_t max_n) {
+    int64_t nb64 = (max_n + 4095) / 4096;
+    return (int)(nb64 < 1 ? 1 : (nb64 > 256 ? 256 : nb64));
+}
+
+// radix_sort_u64 with the digit histogram supplied by the caller
+// (256 * radix_blocks(max_n) uint32 values); allocates nothing.
+int radix_sort_u64_into(uint64_t *keys, uint64_t *tmp, uint32_t *hist, const uint64_t *d_n, int64_t max_n,
+                        int bits_lo, int bits_hi, cudaStream_t st, uint64_t **result) {
+    *result = keys;
+    if (max_n <= 0 || bits_hi <= bits_lo) return FP_OK;
+    const int nb = radix_blocks(max_n);
+    uint64_t *src = keys, *dst = tmp;
+    const uint64_t n_host = (uint64_t)max_n;
+    for (int s = bits_lo; s < bits_hi; s += 8) {
+        int w = bits_hi - s < 8 ? bits_hi - s : 8;
+        uint32_t mask = (1u << w) - 1u;
+        k_radix_hist<<<nb, RB_THREADS, 0, st>>>(src, d_n, n_host, s, mask, hist);
+        FP_LAUNCHED("k_radix_hist");
+        k_scan_u32<<<1, 1024, 0, st>>>(hist, 256 * (int64_t)nb);
+        FP_LAUNCHED("k_scan_u32");
+        k_radix_scatter<<<nb, RB_THREADS, 0, st>>>(src, dst, d_n, n_host, s, mask, hist);
+        FP_LAUNCHED("k_radix_scatter");
+        uint64_t *t = src;
+        src = dst;
+        dst = t;
+    }
+    *result = src;
+    return FP_OK;
+}
+
+// build_csr with caller-supplied sort scratch; allocates nothing.
+int build_csr_into(uint64_t *keys, uint64_t *tmp, uint32_t *hist, const uint64_t *d_n, int64_t max_n, int q_bits,
+                   int idx_bits, int64_t n_queries, int64_t *row_ptr, int32_t *idx, cudaStream_t st) {
+    uint64_t *sorted = keys;
+    FP_TRY(radix_sort_u64_into(keys, tmp, hist, d_n, max_n, 0, q_bits + idx_bits, st, &sorted));
+    int64_t nt = n_queries + 1;
+    k_row_ptr<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(sorted, d_n, (uint64_t)max_n, n_queries, idx_bits,
+                                                            row_ptr);
+    FP_LAUNCHED("k_row_ptr");
+    if (max_n > 0 && idx) {
+        int64_t g = (max_n + 255) / 256;
+        int grid = (int)(g > 4096 ? 4096 : (g < 1 ? 1 : g));
+        k_extract_idx<<<grid, 256, 0, st>>>(sorted, d_n, (uint64_t)max_n, idx_bits, idx);
+        FP_LAUNCHED("k_extract_idx");
+    }
+    return FP_OK;
+}
+
+}  // namespace fpk

@@ -65,6 +65,8 @@ SIGNATURES = {
     "fp_query": (ctypes.c_int, [_VP, _VP, _VP, _I64, _I32, _I32, _VP, ctypes.POINTER(_VP)]),
     "fp_query_ex": (ctypes.c_int, [_VP, _VP, _VP, _I64, _I32, _I32, ctypes.POINTER(fp_query_opts), _VP,
                                    ctypes.POINTER(_VP)]),
+    "fp_query_noalloc": (ctypes.c_int, [_VP, _VP, _VP, _I64, _I32, _I32, _VP, _VP, _I64, ctypes.POINTER(_I64),
+                                        _VP]),
     "fp_result_csr": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I32]),
     "fp_result_stats": (ctypes.c_int, [_VP, ctypes.POINTER(fp_stats)]),
     "fp_result_free": (None, [_VP]),
