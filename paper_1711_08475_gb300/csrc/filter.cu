@@ -29,6 +29,20 @@ constexpr int FT_THREADS = 256;
 constexpr int FT_WARPS = FT_THREADS / 32;
 constexpr int FT_MAX_TQ = 256;
 constexpr int FT_STAGE = 256;  // staged survivors per warp
+constexpr int FT_QUEUE = 256;  // queued (lane, query) hits per warp and 32-query batch
+
+// Tuning constants (compile-time; the defaults come from sweeps on GB300).
+#ifndef FT_MIN_BLOCKS
+#define FT_MIN_BLOCKS 5  // resident blocks per SM the register budget is set for
+#endif
+#ifndef FT_MIX_DIV
+#define FT_MIX_DIV 4  // k = 1 mix: V / FT_MIX_DIV of a thread's words use the ALU-only test
+#endif
+#ifndef FT_UNROLL
+#define FT_UNROLL 2  // groups of four queries unrolled in the hot loop
+#endif
+#define FT_STR(x) #x
+#define FT_UNROLL_PRAGMA(n) _Pragma(FT_STR(unroll n))
 
 // ---------------------------------------------------------------------------
 // tile planner: one block
@@ -208,6 +222,18 @@ __device__ __forceinline__ void flush_stage(const FilterArgs &A, uint64_t *stage
     __syncwarp();
 }
 
+// Appends one survivor to the warp's staging buffer (or, when it is full, to
+// the global list directly).
+__device__ __forceinline__ void stage_push(const FilterArgs &A, uint64_t *stage, uint32_t *cnt, uint64_t e) {
+    const uint32_t pos = atomicAdd(cnt, 1u);
+    if (pos < FT_STAGE) {
+        stage[pos] = e;
+    } else {
+        const unsigned long long g = atomicAdd((unsigned long long *)&A.scal[4], 1ull);
+        if (g < A.surv_cap) A.surv[g] = e;
+    }
+}
+
 // x has at most two bits set: clear the lowest set bit twice (integer ALU
 // only, no population count).  Used for k = 1 on part of a thread's words so
 // that the population-count pipe and the logic pipe share the work.
@@ -231,12 +257,12 @@ __device__ __forceinline__ uint32_t min_tree(const uint32_t *v) {
 // two clears): a spurious hit only costs an exact re-test, a missed pass cannot
 // happen.  K1MIX (32-bit occ/occh/count, k = 1): the last quarter of the words
 // is tested with clear2 instead of the population count (passes iff clear2 == 0,
-// i.e. iff clear2 + 2 <= 2, so it joins the same minimum).
+// i.e. iff (clear2 | 2) <= 2, so it joins the same minimum).
 template <int W, int V, bool POS, bool FULL, bool K1MIX>
 __device__ __forceinline__ int32_t pass_sign(const uint32_t (&w)[V], uint32_t q, const PosMasks &M,
                                              uint32_t invalid, uint32_t T) {
     if (K1MIX) {
-        constexpr int NZ = V / 4, NP = V - NZ;  // NP words through POPC, NZ through clear2
+        constexpr int NZ = V / FT_MIX_DIV, NP = V - NZ;  // NP words through POPC, NZ through clear2
         uint32_t f[NP + 1];
 #pragma unroll
         for (int v = 0; v < NP; v++) {
@@ -246,10 +272,12 @@ __device__ __forceinline__ int32_t pass_sign(const uint32_t (&w)[V], uint32_t q,
         uint32_t z[NZ];
 #pragma unroll
         for (int v = 0; v < NZ; v++) {
-            z[v] = clear2(w[NP + v] ^ q);
-            if (!FULL && ((invalid >> (NP + v)) & 1u)) z[v] = 1u;
+            // clear2 is 0 (pass) or >= 4, so clear2 | 2 is 2 (pass) or >= 6: one
+            // 3-input logic op joins it to the F_D scale
+            z[v] = clear2(w[NP + v] ^ q) | 2u;
+            if (!FULL && ((invalid >> (NP + v)) & 1u)) z[v] = 3u;
         }
-        f[NP] = min_tree<NZ>(z) + 2u;
+        f[NP] = min_tree<NZ>(z);
         return (int32_t)(min_tree<NP + 1>(f) - 3u);
     } else {
         constexpr int NF = (W == 32) ? V : 2 * V;
@@ -279,7 +307,7 @@ __device__ __forceinline__ int32_t pass_sign(const uint32_t (&w)[V], uint32_t q,
 template <int W, int V, bool POS, bool FULL, bool K1MIX>
 __device__ __forceinline__ void scan_tile(const FilterArgs &A, const uint32_t *s_q, uint32_t nq, uint32_t q0,
                                           const uint32_t (&w)[V], uint32_t invalid, uint32_t T, uint32_t wbase,
-                                          uint64_t *stage, uint32_t *cnt, int lane) {
+                                          uint64_t *stage, uint32_t *cnt, uint16_t *queue, int lane) {
     constexpr int G = (W == 32) ? 4 : 8;
     constexpr int NF = (W == 32) ? V : 2 * V;
     const uint4 *s_q4 = reinterpret_cast<const uint4 *>(s_q);
@@ -287,7 +315,7 @@ __device__ __forceinline__ void scan_tile(const FilterArgs &A, const uint32_t *s
         const uint32_t jn = min(32u, nq - jb);
         const uint32_t jn4 = (jn + 3u) & ~3u;
         uint32_t hits = 0;
-#pragma unroll 2
+        FT_UNROLL_PRAGMA(FT_UNROLL)
         for (uint32_t jj = 0; jj < jn; jj += 4) {
             const uint4 q4 = s_q4[(jb + jj) >> 2];
             const int32_t h0 = pass_sign<W, V, POS, FULL, K1MIX>(w, q4.x, A.M, invalid, T);
@@ -300,47 +328,80 @@ __device__ __forceinline__ void scan_tile(const FilterArgs &A, const uint32_t *s
             hits = __funnelshift_l((uint32_t)h3, hits, 1);
         }
         hits &= ~((1u << (jn4 - jn)) - 1u);  // queries past nq in the last group of four
-        // re-test, exactly, the queries that had a (possible) passing fingerprint
-        while (hits) {
-            const uint32_t b = __ffs(hits) - 1;
-            hits &= hits - 1;
-            const uint32_t jj = jn4 - 1u - b;
-            uint32_t F[NF];
-            all_fd<W, V, POS, NF>(w, s_q[jb + jj], A.M, F);
+        // Re-test, exactly, the queries that had a (possible) passing fingerprint.
+        // Every lane posts its (lane, query) hits to the warp's queue; then the
+        // warp's lanes take one hit each and fetch the owner's fingerprints with
+        // shuffles, so the warp spends one round per 32 hits instead of one round
+        // per hit of its busiest lane.
+        const uint32_t c = __popc(hits);
+        uint32_t incl = c;
 #pragma unroll
-            for (int i = 0; i < NF; i++) {
-                if (F[i] <= T && (FULL || !((invalid >> i) & 1u))) {
-                    const uint64_t e = ((uint64_t)(q0 + jb + jj) << 32) | (uint64_t)(wbase + lane_offset<G>(i, lane));
-                    const uint32_t pos = atomicAdd(cnt, 1u);
-                    if (pos < FT_STAGE) {
-                        stage[pos] = e;
-                    } else {  // staging full: reserve a global slot directly
-                        const unsigned long long g = atomicAdd((unsigned long long *)&A.scal[4], 1ull);
-                        if (g < A.surv_cap) A.surv[g] = e;
-                    }
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        if (total != 0 && total <= FT_QUEUE) {
+            uint32_t pos = incl - c;
+            for (uint32_t h = hits; h; h &= h - 1) queue[pos++] = (uint16_t)((lane << 5) | (jn4 - 1u - (__ffs(h) - 1)));
+            __syncwarp();
+            for (uint32_t base = 0; base < total; base += 32) {
+                const uint32_t it = base + lane;
+                const bool has = it < total;
+                const uint32_t item = has ? queue[it] : ((uint32_t)lane << 5);
+                const int src = (int)(item >> 5);
+                const uint32_t jj = item & 31u;
+                uint32_t ws[V];
+#pragma unroll
+                for (int v = 0; v < V; v++) ws[v] = __shfl_sync(0xffffffffu, w[v], src);
+                const uint32_t inv = FULL ? 0u : __shfl_sync(0xffffffffu, invalid, src);
+                if (has) {
+                    uint32_t F[NF];
+                    all_fd<W, V, POS, NF>(ws, s_q[jb + jj], A.M, F);
+#pragma unroll
+                    for (int i = 0; i < NF; i++)
+                        if (F[i] <= T && (FULL || !((inv >> i) & 1u)))
+                            stage_push(A, stage, cnt,
+                                       ((uint64_t)(q0 + jb + jj) << 32) | (uint64_t)(wbase + lane_offset<G>(i, src)));
                 }
             }
+            __syncwarp();
+        } else if (total != 0) {  // very many hits (large k, dense matches): each lane re-tests its own
+            while (hits) {
+                const uint32_t b = __ffs(hits) - 1;
+                hits &= hits - 1;
+                const uint32_t jj = jn4 - 1u - b;
+                uint32_t F[NF];
+                all_fd<W, V, POS, NF>(w, s_q[jb + jj], A.M, F);
+#pragma unroll
+                for (int i = 0; i < NF; i++)
+                    if (F[i] <= T && (FULL || !((invalid >> i) & 1u)))
+                        stage_push(A, stage, cnt,
+                                   ((uint64_t)(q0 + jb + jj) << 32) | (uint64_t)(wbase + lane_offset<G>(i, lane)));
+            }
+            __syncwarp();
         }
-        __syncwarp();
         if (*cnt >= FT_STAGE / 2) flush_stage(A, stage, cnt, lane);
     }
 }
 
 // W: fingerprint width; V: 32-bit words per thread (multiple of 4).
 template <int W, int V, bool POS, bool K1MIX>
-__global__ void __launch_bounds__(FT_THREADS, 5) k_filter_tiled(FilterArgs A) {
+__global__ void __launch_bounds__(FT_THREADS, FT_MIN_BLOCKS) k_filter_tiled(FilterArgs A) {
     constexpr int G = (W == 32) ? 4 : 8;             // fingerprints per 128-bit vector
     constexpr int NF = (W == 32) ? V : 2 * V;        // fingerprints per thread
     constexpr int TW = NF * FT_THREADS;              // fingerprints per tile
     __shared__ __align__(16) uint32_t s_q[FT_MAX_TQ];
     __shared__ uint64_t s_stage[FT_WARPS][FT_STAGE];
     __shared__ uint32_t s_cnt[FT_WARPS];
+    __shared__ uint16_t s_queue[FT_WARPS][FT_QUEUE];
     __shared__ uint64_t s_tile;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nseg = (int)A.scal[0];
     const uint64_t ntiles = A.scal[1];
     uint64_t *stage = s_stage[warp];
     uint32_t *cnt = &s_cnt[warp];
+    uint16_t *queue = s_queue[warp];
     if (lane == 0) *cnt = 0;
     __syncwarp();
     for (;;) {
@@ -382,13 +443,13 @@ __global__ void __launch_bounds__(FT_THREADS, 5) k_filter_tiled(FilterArgs A) {
             if (lane_offset<G>(i, lane) >= nvalid) invalid |= 1u << i;
         if (K1MIX && T != 2u) {  // a k = 1 variant given another k: exact general path
             if (nw == (uint32_t)TW)
-                scan_tile<W, V, POS, true, false>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, lane);
+                scan_tile<W, V, POS, true, false>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, queue, lane);
             else
-                scan_tile<W, V, POS, false, false>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, lane);
+                scan_tile<W, V, POS, false, false>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, queue, lane);
         } else if (nw == (uint32_t)TW) {
-            scan_tile<W, V, POS, true, K1MIX>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, lane);
+            scan_tile<W, V, POS, true, K1MIX>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, queue, lane);
         } else {
-            scan_tile<W, V, POS, false, K1MIX>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, lane);
+            scan_tile<W, V, POS, false, K1MIX>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, queue, lane);
         }
         __syncthreads();
     }
