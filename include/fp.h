@@ -151,6 +151,41 @@ FP_API int fp_query(fp_index *ix, const uint8_t *chars, const int64_t *offsets, 
 FP_API int fp_query_ex(fp_index *ix, const uint8_t *chars, const int64_t *offsets, int64_t n_queries, int k,
                 int metric, const fp_query_opts *opts, void *cuda_stream, fp_result **out);
 
+/* ---- batched queries and captured plans --------------------------------- */
+/* The paper answers one pattern at a time (Sec. 4: the query fingerprint is
+ * built once and compared with every word).  These entry points answer many
+ * batches, each with its own k and metric, in one pass: patterns are bucketed
+ * by (k, metric, length), and one persistent kernel filters (Eq. 1) and
+ * verifies (Sec. 4) every tile of every batch.  Batches are consecutive
+ * ranges of the pattern list (batch b covers the next batches[b].n_queries
+ * patterns); the result is one CSR over all patterns in input order. */
+typedef struct {
+    int64_t n_queries;
+    int32_t k;      /* 0..15 */
+    int32_t metric; /* fp_metric */
+} fp_batch;
+typedef struct fp_plan fp_plan;
+
+/* One-off batched query (no graph).  chars, offsets: host or device;
+ * batches: host.  Errors as fp_query; FP_E_INVAL if the batch sizes do not
+ * add up to n_queries.  Synchronises cuda_stream. */
+FP_API int fp_query_batched(fp_index *ix, const uint8_t *chars, const int64_t *offsets, int64_t n_queries,
+                            const fp_batch *batches, int32_t n_batches, const fp_query_opts *opts, void *cuda_stream,
+                            fp_result **out);
+/* A plan owns every device buffer for up to max_queries patterns of
+ * max_chars bytes in max_batches batches (allocated here, once).  The first
+ * fp_plan_run of a shape (patterns, bytes, batches, distinct (k, metric)
+ * groups) records the device pipeline into a CUDA graph on the plan's own
+ * stream; later runs of the same shape replay it with one graph launch.
+ * opts: tile_queries and variant as for fp_query_ex; mode FP_MODE_PLAIN turns
+ * the graph off.  Runs of one plan must not overlap (one host thread at a
+ * time); results do not refer to the plan's memory. */
+FP_API int fp_plan_create(fp_index *ix, int64_t max_queries, int64_t max_chars, int32_t max_batches,
+                          const fp_query_opts *opts, fp_plan **out);
+FP_API int fp_plan_run(fp_plan *plan, const uint8_t *chars, const int64_t *offsets, int64_t n_queries,
+                       const fp_batch *batches, int32_t n_batches, void *cuda_stream, fp_result **out);
+FP_API void fp_plan_free(fp_plan *plan);
+
 /* ---- query without device allocation ------------------------------------ */
 /* The paper has no counterpart to this entry point: it is a deployment aid.
  * Same result as fp_query for small batches, but the call allocates no device

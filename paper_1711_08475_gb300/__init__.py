@@ -196,6 +196,70 @@ def fp_query(index: Index, chars, offsets=None, k: int = 1, metric: str = "ham",
     return fp_query_ex(index, chars, offsets, k, metric, stream=stream)
 
 
+def _batches(batches):
+    """[(n_queries, k, metric), ...] -> ctypes array of fp_batch."""
+    arr = (native.fp_batch * len(batches))()
+    for i, (n, k, metric) in enumerate(batches):
+        arr[i].n_queries = int(n)
+        arr[i].k = int(k)
+        arr[i].metric = METRICS[metric] if isinstance(metric, str) else int(metric)
+    return arr
+
+
+def fp_query_batched(index: Index, chars, offsets=None, batches=(), tile_queries: int = 0, variant: int = 0,
+                     stream=None) -> Result:
+    """Many batches with their own (k, metric) in one pass (fp_query_batched)."""
+    L = load()
+    chars, offsets, n = _strings(chars, offsets)
+    o = native.fp_query_opts()
+    o.tile_queries = tile_queries
+    o.variant = variant
+    b = _batches(batches)
+    cp, k1 = _ptr(chars)
+    op, k2 = _ptr(offsets)
+    h = ctypes.c_void_p()
+    check(L.fp_query_batched(index._h, cp, op, n, ctypes.cast(b, ctypes.c_void_p), len(b), ctypes.byref(o),
+                             _stream(stream), ctypes.byref(h)), "fp_query_batched")
+    return Result(h.value, n)
+
+
+class Plan:
+    """Buffers and a captured CUDA graph for repeated batched queries (fp_plan_*)."""
+
+    def __init__(self, index: Index, max_queries: int, max_chars: int, max_batches: int, tile_queries: int = 0,
+                 variant: int = 0, graph: bool = True):
+        o = native.fp_query_opts()
+        o.mode = FP_MODE_FUSED if graph else FP_MODE_PLAIN
+        o.tile_queries = tile_queries
+        o.variant = variant
+        h = ctypes.c_void_p()
+        check(load().fp_plan_create(index._h, max_queries, max_chars, max_batches, ctypes.byref(o), ctypes.byref(h)),
+              "fp_plan_create")
+        self._h = h.value
+        self.index = index
+
+    def run(self, chars, offsets=None, batches=(), stream=None) -> Result:
+        chars, offsets, n = _strings(chars, offsets)
+        b = _batches(batches)
+        cp, k1 = _ptr(chars)
+        op, k2 = _ptr(offsets)
+        h = ctypes.c_void_p()
+        check(load().fp_plan_run(self._h, cp, op, n, ctypes.cast(b, ctypes.c_void_p), len(b), _stream(stream),
+                                 ctypes.byref(h)), "fp_plan_run")
+        return Result(h.value, n)
+
+    def free(self):
+        if self._h:
+            load().fp_plan_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
 def fp_launch_count() -> int:
     return int(load().fp_launch_count())
 

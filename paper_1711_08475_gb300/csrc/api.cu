@@ -58,12 +58,12 @@ int sm_count() {
     return n;
 }
 
-static int fail(int code, const std::string &msg) {
+int fail(int code, const std::string &msg) {
     t_err = msg;
     return code;
 }
 
-static bool is_device_ptr(const void *p) {
+bool is_device_ptr(const void *p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
@@ -72,14 +72,14 @@ static bool is_device_ptr(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-static int bits_for(int64_t n) {  // bits to hold values 0 .. n-1 (at least 1)
+int bits_for(int64_t n) {  // bits to hold values 0 .. n-1 (at least 1)
     int b = 1;
     while (b < 63 && ((int64_t)1 << b) < n) b++;
     return b;
 }
 
 // Validates host offsets: offsets[0] == 0, non-decreasing, lengths <= 255.
-static int check_host_offsets(const int64_t *off, int64_t n) {
+int check_host_offsets(const int64_t *off, int64_t n) {
     if (off[0] != 0) return fail(FP_E_INVAL, "offsets[0] must be 0");
     for (int64_t i = 0; i < n; i++) {
         int64_t L = off[i + 1] - off[i];
@@ -144,17 +144,6 @@ static int stage_strings(const uint8_t *chars, const int64_t *off, int64_t n, cu
 
 using namespace fpk;
 
-
-struct fp_result {
-    int64_t n_queries = 0;
-    int64_t n_matches = 0;
-    int64_t *d_row_ptr = nullptr;
-    int32_t *d_idx = nullptr;
-    std::vector<int64_t> h_row_ptr;
-    std::vector<int32_t> h_idx;
-    bool host_ready = false;
-    fp_stats stats{};
-};
 
 extern "C" {
 
@@ -374,7 +363,8 @@ int fp_query_ex(fp_index *ix, const uint8_t *chars, const int64_t *offsets, int6
         return fail(FP_E_UNSUPPORTED, "occurrence-halved and position fingerprints bound only the Hamming distance");
     fp_query_opts o{};
     if (opts) o = *opts;
-    if (o.mode != FP_MODE_TILED && o.mode != FP_MODE_PLAIN) return fail(FP_E_UNSUPPORTED, "query mode not available");
+    if (o.mode != FP_MODE_TILED && o.mode != FP_MODE_PLAIN && o.mode != FP_MODE_FUSED)
+        return fail(FP_E_UNSUPPORTED, "query mode not available");
     FilterCfg cfg;
     cfg.mode = o.mode;
     // defaults from a sweep on the 1M-word English-like workload: 4 words per
@@ -382,6 +372,8 @@ int fp_query_ex(fp_index *ix, const uint8_t *chars, const int64_t *offsets, int6
     cfg.v = o.words_per_thread == 8 ? 8 : 4;
     cfg.tq = o.mode == FP_MODE_PLAIN ? 1 : (o.tile_queries > 0 ? std::min(o.tile_queries, 256) : 256);
     cfg.k1mix = o.variant == 0 && k == 1;
+    const bool fused = o.mode == FP_MODE_FUSED;
+    if (fused) cfg.v = 4;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     init_pool();
 
@@ -455,6 +447,7 @@ int fp_query_ex(fp_index *ix, const uint8_t *chars, const int64_t *offsets, int6
         1, std::min<int64_t>(pairs_bound, std::max<int64_t>(1 << 20, (int64_t)(pairs_bound * ix->surv_ratio * 1.5))));
     R.match_cap = std::max<int64_t>(1, std::min<int64_t>(R.surv_cap, std::max<int64_t>(1 << 20, n_queries * 64)));
     CK(cudaEventRecord(R.ev[1], st));
+    if (fused) R.surv_cap = 1;  // the fused form keeps survivors on chip
     for (int attempt = 0; attempt < 2; attempt++) {
         CK(cudaMallocAsync((void **)&R.surv, sizeof(uint64_t) * (size_t)R.surv_cap, st));
         CK(cudaMallocAsync((void **)&R.matches, sizeof(uint64_t) * (size_t)R.match_cap, st));
@@ -462,10 +455,16 @@ int fp_query_ex(fp_index *ix, const uint8_t *chars, const int64_t *offsets, int6
             CK(cudaMemsetAsync(R.plan.scal + 3, 0, 3 * sizeof(uint64_t), st));
             CK(cudaEventRecord(R.ev[1], st));
         }
-        TRY(launch_filter(R.Q, ix->D, R.plan, ix->P, cfg, R.surv, R.surv_cap, st, &res->stats.filter_launches));
-        CK(cudaEventRecord(R.ev[2], st));
-        TRY(launch_verify(R.Q, ix->D, R.surv, R.plan.scal + 4, R.surv_cap, k, metric, idx_bits, R.matches,
-                          R.plan.scal + 5, R.match_cap, st));
+        if (fused) {
+            TRY(launch_fused(R.Q, ix->D, R.plan, ix->P, cfg, idx_bits, R.matches, R.match_cap, st,
+                             &res->stats.filter_launches));
+            CK(cudaEventRecord(R.ev[2], st));
+        } else {
+            TRY(launch_filter(R.Q, ix->D, R.plan, ix->P, cfg, R.surv, R.surv_cap, st, &res->stats.filter_launches));
+            CK(cudaEventRecord(R.ev[2], st));
+            TRY(launch_verify(R.Q, ix->D, R.surv, R.plan.scal + 4, R.surv_cap, k, metric, idx_bits, R.matches,
+                              R.plan.scal + 5, R.match_cap, st));
+        }
         CK(cudaEventRecord(R.ev[3], st));
         // result buffers sized by the match capacity; the sort borrows the survivor buffer
         if (!res->d_row_ptr)
@@ -501,14 +500,14 @@ int fp_query_ex(fp_index *ix, const uint8_t *chars, const int64_t *offsets, int6
             rc = fail(FP_E_NOMEM, "tile plan overflow");
             goto done;
         }
-        if ((int64_t)scal[4] <= R.surv_cap && (int64_t)scal[5] <= R.match_cap) break;
+        if ((fused || (int64_t)scal[4] <= R.surv_cap) && (int64_t)scal[5] <= R.match_cap) break;
         // too small: redo filter, verify and emit with exact sizes.  After a
         // survivor overflow only part of the survivors were verified, so the
         // match count is a lower bound and the survivor count bounds it.
         cudaFreeAsync(R.surv, st);
         cudaFreeAsync(R.matches, st);
         R.surv = R.matches = nullptr;
-        if ((int64_t)scal[4] > R.surv_cap) {
+        if (!fused && (int64_t)scal[4] > R.surv_cap) {
             R.surv_cap = std::max<int64_t>(1, (int64_t)scal[4]);
             R.match_cap = R.surv_cap;
         } else {

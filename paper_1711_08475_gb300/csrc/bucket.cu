@@ -505,12 +505,12 @@ int refingerprint(Bucketed *B, const int8_t *d_map, const FpParams &P, cudaStrea
 namespace fpk {
 
 // bucketize() into arrays the caller has placed in B (fp, idx, len, row16,
-// str, b_start, b_count, sized for n strings of total_chars bytes and 256
-// length bins) with the temporaries in S; allocates nothing.  One group only.
+// str, b_start, b_count, sized for n strings of total_chars bytes and
+// 256 * n_groups bins) with the temporaries in S; allocates nothing.
 int bucketize_into(const uint8_t *d_chars, const int64_t *d_off, int64_t n, int64_t total_chars,
-                   const int8_t *d_map, const FpParams &P, cudaStream_t st, Bucketed *B, const BucketScratch &S,
-                   int32_t *d_err) {
-    const int nbins = 256;
+                   const int32_t *d_group, int32_t n_groups, const int8_t *d_map, const FpParams &P, cudaStream_t st,
+                   Bucketed *B, const BucketScratch &S, int32_t *d_err) {
+    const int nbins = 256 * (n_groups < 1 ? 1 : n_groups);
     const int64_t slots_ub = n + (int64_t)(SLOT_ALIGN - 1) * nbins;
     const int64_t str_ub = total_chars + 15 * n;
     const size_t fpw = P.width == 16 ? 2 : 4;
@@ -524,15 +524,17 @@ int bucketize_into(const uint8_t *d_chars, const int64_t *d_off, int64_t n, int6
     FP_CUDA(cudaMemsetAsync(B->str + str_ub, 0, STR_SLACK, st));
     FP_CUDA(cudaMemsetAsync(S.hist, 0, nbins * 4, st));
     if (n > 0) {
-        int g = grid_for(n, 256, 2048);
-        k_bin_keys<<<g, 256, nbins * sizeof(int32_t), st>>>(d_off, n, nullptr, nbins, S.keys, S.hist, d_err);
+        const int g = grid_for(n, 256, 2048);
+        k_bin_keys<<<g, 256, nbins * sizeof(int32_t), st>>>(d_off, n, d_group, nbins, S.keys, S.hist, d_err);
         FP_LAUNCHED("k_bin_keys");
     }
     k_plan_bins<<<1, 1024, 0, st>>>(S.hist, nbins, B->b_start, B->b_count, S.ustart, S.str16, S.tot);
     FP_LAUNCHED("k_plan_bins");
     if (n > 0) {
+        int bin_bits = 1;
+        while ((1 << bin_bits) < nbins) bin_bits++;
         uint64_t *sorted = S.keys;
-        FP_TRY(radix_sort_u64_into(S.keys, S.keys2, S.radix_hist, nullptr, n, 32, 40, st, &sorted));
+        FP_TRY(radix_sort_u64_into(S.keys, S.keys2, S.radix_hist, nullptr, n, 32, 32 + bin_bits, st, &sorted));
         int g = grid_for(n, 256, 8192);
         switch (P.type) {
             case FP_OCC:

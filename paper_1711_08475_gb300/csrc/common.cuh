@@ -6,6 +6,7 @@
 
 #include <atomic>
 #include <string>
+#include <vector>
 
 #include "fp.h"
 
@@ -138,6 +139,13 @@ int launch_filter(const Bucketed &q, const Bucketed &d, const QueryPlan &plan, c
                   const FilterCfg &cfg, uint64_t *surv, int64_t surv_cap, cudaStream_t st,
                   int64_t *launches);
 
+// Filter and verification in one persistent kernel: survivors never leave
+// the SM; matches (original query << idx_bits | original word) are appended
+// to `matches` (counter plan.scal[5]; plan.scal[4] counts the survivors).
+int launch_fused(const Bucketed &q, const Bucketed &d, const QueryPlan &plan, const FpParams &fp,
+                 const FilterCfg &cfg, int idx_bits, uint64_t *matches, int64_t match_cap, cudaStream_t st,
+                 int64_t *launches);
+
 int launch_verify(const Bucketed &q, const Bucketed &d, const uint64_t *surv, const uint64_t *d_n_surv,
                   int64_t surv_cap, int k, int metric, int idx_bits, uint64_t *matches,
                   uint64_t *d_n_matches, int64_t match_cap, cudaStream_t st);
@@ -149,6 +157,11 @@ int build_csr(uint64_t *keys, uint64_t *tmp, const uint64_t *d_n, int64_t max_n,
               int64_t n_queries, int64_t *row_ptr, int32_t *idx, cudaStream_t st);
 
 int sm_count();
+void init_pool();
+int fail(int code, const std::string &msg);
+bool is_device_ptr(const void *p);
+int bits_for(int64_t n);
+int check_host_offsets(const int64_t *off, int64_t n);
 
 // ---------------------------------------------------------------------------
 // the same steps on caller-placed buffers (nothing is allocated)
@@ -166,10 +179,26 @@ int radix_sort_u64_into(uint64_t *keys, uint64_t *tmp, uint32_t *hist, const uin
 int build_csr_into(uint64_t *keys, uint64_t *tmp, uint32_t *hist, const uint64_t *d_n, int64_t max_n, int q_bits,
                    int idx_bits, int64_t n_queries, int64_t *row_ptr, int32_t *idx, cudaStream_t st);
 int bucketize_into(const uint8_t *d_chars, const int64_t *d_off, int64_t n, int64_t total_chars,
-                   const int8_t *d_map, const FpParams &P, cudaStream_t st, Bucketed *B, const BucketScratch &S,
-                   int32_t *d_err);
+                   const int32_t *d_group, int32_t n_groups, const int8_t *d_map, const FpParams &P, cudaStream_t st,
+                   Bucketed *B, const BucketScratch &S, int32_t *d_err);
+// group[i] = batch_group[b] for every pattern i of batch b (batch b covers
+// [batch_start[b], batch_start[b+1]), device arrays).
+int fill_groups(const int64_t *d_batch_start, const int32_t *d_batch_group, int n_batches, int32_t *d_group,
+                cudaStream_t st);
 
 }  // namespace fpk
+
+// Match lists behind the opaque fp_result handle.
+struct fp_result {
+    int64_t n_queries = 0;
+    int64_t n_matches = 0;
+    int64_t *d_row_ptr = nullptr;  // stream-ordered pool memory
+    int32_t *d_idx = nullptr;
+    std::vector<int64_t> h_row_ptr;
+    std::vector<int32_t> h_idx;
+    bool host_ready = false;
+    fp_stats stats{};
+};
 
 // The resident dictionary behind the opaque fp_index handle.
 struct fp_index {

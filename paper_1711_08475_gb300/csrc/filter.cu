@@ -21,7 +21,7 @@
 // queries each thread re-tests just the queries whose bit is set and appends
 // the passing pairs to a per-warp buffer in shared memory.  A full buffer is
 // flushed to the global survivor list with one atomic reservation per flush.
-#include "common.cuh"
+#include "verify_core.cuh"
 
 namespace fpk {
 
@@ -166,12 +166,63 @@ struct FilterArgs {
     const uint16_t *qfp16;  // query fingerprints (16-bit slots)
     const uint32_t *dfp;    // dictionary fingerprints viewed as 32-bit words
     const Segment *seg;
-    uint64_t *scal;         // [0] n_seg [1] tiles [3] tile counter [4] survivors
+    uint64_t *scal;         // [0] n_seg [1] tiles [3] tile counter [4] survivors [5] matches
     uint64_t *surv;
     uint64_t surv_cap;
     PosMasks M;
     int tq;
+    // fused form: survivors are verified in the kernel and only matches leave it
+    const uint8_t *q_len, *d_len;
+    const uint32_t *q_row16, *d_row16;
+    const uint8_t *q_str, *d_str;
+    const int32_t *q_idx, *d_idx;
+    int idx_bits;
+    uint64_t *matches;
+    uint64_t match_cap;
 };
+
+// Explicit check of one surviving pair (Sec. 4): Hamming for equal lengths,
+// banded Levenshtein otherwise.  Returns the match key (original query index
+// << idx_bits | original word index) through *key.
+static __device__ __noinline__ bool verify_one(const FilterArgs &A, uint64_t e, int k, int metric,
+                                               uint64_t *key) {
+    const uint32_t qs = (uint32_t)(e >> 32), ds = (uint32_t)e;
+    const int m = A.q_len[qs], L = A.d_len[ds];
+    const uint8_t *qa = A.q_str + (uint64_t)A.q_row16[qs] * 16;
+    const uint8_t *da = A.d_str + (uint64_t)A.d_row16[ds] * 16;
+    const bool hit = metric == FP_HAM ? (m == L && ham_within(qa, da, m, k))
+                                      : (m - L <= k && L - m <= k && lev_within_k(k, qa, m, da, L));
+    *key = ((uint64_t)(uint32_t)A.q_idx[qs] << A.idx_bits) | (uint64_t)(uint32_t)A.d_idx[ds];
+    return hit;
+}
+
+// Fused form: verifies the warp's staged survivors, one per lane, and
+// appends the matches with one reservation per round of 32.
+__device__ __forceinline__ void verify_stage(const FilterArgs &A, uint64_t *stage, uint32_t *cnt, int lane, int k,
+                                             int metric) {
+    __syncwarp();
+    const uint32_t c = min(*cnt, (uint32_t)FT_STAGE);
+    const unsigned lt = (1u << lane) - 1u;
+    if (lane == 0 && c) atomicAdd((unsigned long long *)&A.scal[4], (unsigned long long)c);
+    for (uint32_t base = 0; base < c; base += 32) {
+        const uint32_t i = base + lane;
+        uint64_t key = 0;
+        const bool hit = i < c && verify_one(A, stage[i], k, metric, &key);
+        const unsigned bal = __ballot_sync(0xffffffffu, hit);
+        if (bal) {
+            unsigned long long mb = 0;
+            if (lane == 0) mb = atomicAdd((unsigned long long *)&A.scal[5], (unsigned long long)__popc(bal));
+            mb = __shfl_sync(0xffffffffu, mb, 0);
+            if (hit) {
+                const uint64_t pos = mb + __popc(bal & lt);
+                if (pos < A.match_cap) A.matches[pos] = key;
+            }
+        }
+    }
+    __syncwarp();
+    if (lane == 0) *cnt = 0;
+    __syncwarp();
+}
 
 __device__ __forceinline__ int find_segment(const Segment *seg, int nseg, uint64_t tile) {
     int lo = 0, hi = nseg - 1;
@@ -222,15 +273,25 @@ __device__ __forceinline__ void flush_stage(const FilterArgs &A, uint64_t *stage
     __syncwarp();
 }
 
-// Appends one survivor to the warp's staging buffer (or, when it is full, to
-// the global list directly).
-__device__ __forceinline__ void stage_push(const FilterArgs &A, uint64_t *stage, uint32_t *cnt, uint64_t e) {
+// Appends one survivor to the warp's staging buffer.  When it is full the
+// survivor goes to the global list directly, or, in the fused form, is
+// verified on the spot by this thread.
+template <bool FUSED>
+__device__ __forceinline__ void stage_push(const FilterArgs &A, uint64_t *stage, uint32_t *cnt, uint64_t e, int k,
+                                           int metric) {
     const uint32_t pos = atomicAdd(cnt, 1u);
     if (pos < FT_STAGE) {
         stage[pos] = e;
-    } else {
+    } else if (!FUSED) {
         const unsigned long long g = atomicAdd((unsigned long long *)&A.scal[4], 1ull);
         if (g < A.surv_cap) A.surv[g] = e;
+    } else {
+        atomicAdd((unsigned long long *)&A.scal[4], 1ull);
+        uint64_t key;
+        if (verify_one(A, e, k, metric, &key)) {
+            const unsigned long long g = atomicAdd((unsigned long long *)&A.scal[5], 1ull);
+            if (g < A.match_cap) A.matches[g] = key;
+        }
     }
 }
 
@@ -304,10 +365,11 @@ __device__ __forceinline__ int32_t pass_sign(const uint32_t (&w)[V], uint32_t q,
 // Query fingerprints are read four at a time (one 128-bit shared load), the
 // four tests are independent, and each test's sign bit is shifted into the
 // hit mask (bit b of a 32-query batch <-> query jn4 - 1 - b).
-template <int W, int V, bool POS, bool FULL, bool K1MIX>
+template <int W, int V, bool POS, bool FULL, bool K1MIX, bool FUSED>
 __device__ __forceinline__ void scan_tile(const FilterArgs &A, const uint32_t *s_q, uint32_t nq, uint32_t q0,
                                           const uint32_t (&w)[V], uint32_t invalid, uint32_t T, uint32_t wbase,
-                                          uint64_t *stage, uint32_t *cnt, uint16_t *queue, int lane) {
+                                          uint64_t *stage, uint32_t *cnt, uint16_t *queue, int lane, int k,
+                                          int metric) {
     constexpr int G = (W == 32) ? 4 : 8;
     constexpr int NF = (W == 32) ? V : 2 * V;
     const uint4 *s_q4 = reinterpret_cast<const uint4 *>(s_q);
@@ -361,8 +423,9 @@ __device__ __forceinline__ void scan_tile(const FilterArgs &A, const uint32_t *s
 #pragma unroll
                     for (int i = 0; i < NF; i++)
                         if (F[i] <= T && (FULL || !((inv >> i) & 1u)))
-                            stage_push(A, stage, cnt,
-                                       ((uint64_t)(q0 + jb + jj) << 32) | (uint64_t)(wbase + lane_offset<G>(i, src)));
+                            stage_push<FUSED>(A, stage, cnt,
+                                              ((uint64_t)(q0 + jb + jj) << 32) | (uint64_t)(wbase + lane_offset<G>(i, src)),
+                                              k, metric);
                 }
             }
             __syncwarp();
@@ -376,17 +439,21 @@ __device__ __forceinline__ void scan_tile(const FilterArgs &A, const uint32_t *s
 #pragma unroll
                 for (int i = 0; i < NF; i++)
                     if (F[i] <= T && (FULL || !((invalid >> i) & 1u)))
-                        stage_push(A, stage, cnt,
-                                   ((uint64_t)(q0 + jb + jj) << 32) | (uint64_t)(wbase + lane_offset<G>(i, lane)));
+                        stage_push<FUSED>(A, stage, cnt,
+                                          ((uint64_t)(q0 + jb + jj) << 32) | (uint64_t)(wbase + lane_offset<G>(i, lane)),
+                                          k, metric);
             }
             __syncwarp();
         }
-        if (*cnt >= FT_STAGE / 2) flush_stage(A, stage, cnt, lane);
+        if (*cnt >= FT_STAGE / 2) {
+            if (FUSED) verify_stage(A, stage, cnt, lane, k, metric);
+            else flush_stage(A, stage, cnt, lane);
+        }
     }
 }
 
 // W: fingerprint width; V: 32-bit words per thread (multiple of 4).
-template <int W, int V, bool POS, bool K1MIX>
+template <int W, int V, bool POS, bool K1MIX, bool FUSED>
 __global__ void __launch_bounds__(FT_THREADS, FT_MIN_BLOCKS) k_filter_tiled(FilterArgs A) {
     constexpr int G = (W == 32) ? 4 : 8;             // fingerprints per 128-bit vector
     constexpr int NF = (W == 32) ? V : 2 * V;        // fingerprints per thread
@@ -443,67 +510,110 @@ __global__ void __launch_bounds__(FT_THREADS, FT_MIN_BLOCKS) k_filter_tiled(Filt
             if (lane_offset<G>(i, lane) >= nvalid) invalid |= 1u << i;
         if (K1MIX && T != 2u) {  // a k = 1 variant given another k: exact general path
             if (nw == (uint32_t)TW)
-                scan_tile<W, V, POS, true, false>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, queue, lane);
+                scan_tile<W, V, POS, true, false, FUSED>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, queue, lane,
+                                                           S.k, S.metric);
             else
-                scan_tile<W, V, POS, false, false>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, queue, lane);
+                scan_tile<W, V, POS, false, false, FUSED>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, queue, lane,
+                                                           S.k, S.metric);
         } else if (nw == (uint32_t)TW) {
-            scan_tile<W, V, POS, true, K1MIX>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, queue, lane);
+            scan_tile<W, V, POS, true, K1MIX, FUSED>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, queue, lane,
+                                                           S.k, S.metric);
         } else {
-            scan_tile<W, V, POS, false, K1MIX>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, queue, lane);
+            scan_tile<W, V, POS, false, K1MIX, FUSED>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, queue, lane,
+                                                           S.k, S.metric);
         }
+        // fused: the next tile may have another (k, metric), so verify what is staged
+        if (FUSED) verify_stage(A, stage, cnt, lane, S.k, S.metric);
         __syncthreads();
     }
-    flush_stage(A, stage, cnt, lane);
+    if (!FUSED) flush_stage(A, stage, cnt, lane);
 }
 
-template <int W, int V, bool POS>
+template <int W, int V, bool POS, bool FUSED>
 static int launch_one(const FilterArgs &A, bool k1mix, cudaStream_t st) {
     static int grid[2] = {0, 0};
     int &g = grid[k1mix ? 1 : 0];
     if (g == 0) {
         int per_sm = 0;
         if (k1mix)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_tiled<W, V, POS, (W == 32 && !POS)>,
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_tiled<W, V, POS, (W == 32 && !POS), FUSED>,
                                                           FT_THREADS, 0);
         else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_tiled<W, V, POS, false>, FT_THREADS, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_tiled<W, V, POS, false, FUSED>, FT_THREADS,
+                                                          0);
         g = sm_count() * (per_sm > 0 ? per_sm : 1);
     }
-    if (k1mix) k_filter_tiled<W, V, POS, (W == 32 && !POS)><<<g, FT_THREADS, 0, st>>>(A);
-    else k_filter_tiled<W, V, POS, false><<<g, FT_THREADS, 0, st>>>(A);
-    FP_LAUNCHED("k_filter_tiled");
+    if (k1mix) k_filter_tiled<W, V, POS, (W == 32 && !POS), FUSED><<<g, FT_THREADS, 0, st>>>(A);
+    else k_filter_tiled<W, V, POS, false, FUSED><<<g, FT_THREADS, 0, st>>>(A);
+    FP_LAUNCHED(FUSED ? "k_filter_tiled(fused)" : "k_filter_tiled");
     return FP_OK;
+}
+
+template <bool FUSED>
+static int dispatch(const FilterArgs &A, const FpParams &fp, const FilterCfg &cfg, cudaStream_t st) {
+    const bool pos = fp.type == FP_POS;
+    // the mixed POPC / ALU test applies to 32-bit popcount-type fingerprints at k = 1
+    const bool mix = cfg.k1mix && fp.width == 32 && !pos;
+    if (FUSED) {  // the fused form is built for 4 words per thread only
+        if (fp.width == 32)
+            return pos ? launch_one<32, 4, true, true>(A, false, st) : launch_one<32, 4, false, true>(A, mix, st);
+        return pos ? launch_one<16, 4, true, true>(A, false, st) : launch_one<16, 4, false, true>(A, false, st);
+    }
+    if (fp.width == 32) {
+        if (cfg.v == 4)
+            return pos ? launch_one<32, 4, true, false>(A, false, st) : launch_one<32, 4, false, false>(A, mix, st);
+        return pos ? launch_one<32, 8, true, false>(A, false, st) : launch_one<32, 8, false, false>(A, mix, st);
+    }
+    if (cfg.v == 4)
+        return pos ? launch_one<16, 4, true, false>(A, false, st) : launch_one<16, 4, false, false>(A, false, st);
+    return pos ? launch_one<16, 8, true, false>(A, false, st) : launch_one<16, 8, false, false>(A, false, st);
 }
 
 int tile_words(int width, int v) { return (width == 32 ? v : 2 * v) * FT_THREADS; }
 
-int launch_filter(const Bucketed &q, const Bucketed &d, const QueryPlan &plan, const FpParams &fp,
-                  const FilterCfg &cfg, uint64_t *surv, int64_t surv_cap, cudaStream_t st,
-                  int64_t *launches) {
-    FilterArgs A;
+static FilterArgs make_args(const Bucketed &q, const Bucketed &d, const QueryPlan &plan, const FpParams &fp,
+                            const FilterCfg &cfg) {
+    FilterArgs A{};
     A.qfp32 = (const uint32_t *)q.fp;
     A.qfp16 = (const uint16_t *)q.fp;
     A.dfp = (const uint32_t *)d.fp;
     A.seg = plan.seg;
     A.scal = plan.scal;
-    A.surv = surv;
-    A.surv_cap = (uint64_t)surv_cap;
     const bool rep = fp.width == 16;
     A.M.low = fp.pos_low | (rep ? fp.pos_low << 16 : 0u);
     A.M.high = fp.pos_high | (rep ? fp.pos_high << 16 : 0u);
     A.M.occ = fp.pos_occ | (rep ? fp.pos_occ << 16 : 0u);
     A.tq = cfg.tq < 1 ? 1 : (cfg.tq > FT_MAX_TQ ? FT_MAX_TQ : cfg.tq);
-    const bool pos = fp.type == FP_POS;
-    // the mixed POPC / ALU test applies to 32-bit popcount-type fingerprints at k = 1
-    const bool mix = cfg.k1mix && fp.width == 32 && !pos;
-    int rc;
-    if (fp.width == 32) {
-        if (cfg.v == 4) rc = pos ? launch_one<32, 4, true>(A, false, st) : launch_one<32, 4, false>(A, mix, st);
-        else rc = pos ? launch_one<32, 8, true>(A, false, st) : launch_one<32, 8, false>(A, mix, st);
-    } else {
-        if (cfg.v == 4) rc = pos ? launch_one<16, 4, true>(A, false, st) : launch_one<16, 4, false>(A, false, st);
-        else rc = pos ? launch_one<16, 8, true>(A, false, st) : launch_one<16, 8, false>(A, false, st);
-    }
+    return A;
+}
+
+int launch_filter(const Bucketed &q, const Bucketed &d, const QueryPlan &plan, const FpParams &fp,
+                  const FilterCfg &cfg, uint64_t *surv, int64_t surv_cap, cudaStream_t st,
+                  int64_t *launches) {
+    FilterArgs A = make_args(q, d, plan, fp, cfg);
+    A.surv = surv;
+    A.surv_cap = (uint64_t)surv_cap;
+    int rc = dispatch<false>(A, fp, cfg, st);
+    if (launches) (*launches)++;
+    return rc;
+}
+
+int launch_fused(const Bucketed &q, const Bucketed &d, const QueryPlan &plan, const FpParams &fp,
+                 const FilterCfg &cfg, int idx_bits, uint64_t *matches, int64_t match_cap, cudaStream_t st,
+                 int64_t *launches) {
+    FilterArgs A = make_args(q, d, plan, fp, cfg);
+    A.q_len = q.len;
+    A.d_len = d.len;
+    A.q_row16 = q.row16;
+    A.d_row16 = d.row16;
+    A.q_str = q.str;
+    A.d_str = d.str;
+    A.q_idx = q.idx;
+    A.d_idx = d.idx;
+    A.idx_bits = idx_bits;
+    A.matches = matches;
+    A.match_cap = (uint64_t)match_cap;
+    int rc = dispatch<true>(A, fp, cfg, st);
     if (launches) (*launches)++;
     return rc;
 }

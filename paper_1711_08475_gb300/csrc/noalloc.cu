@@ -172,7 +172,7 @@ extern "C" int fp_query_noalloc(fp_index *ix, const uint8_t *chars, const int64_
     const int32_t group[2] = {k, metric};
     FP_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int32_t), st));
     FP_CUDA(cudaMemcpyAsync(d_group, group, sizeof(group), cudaMemcpyHostToDevice, st));
-    FP_TRY(bucketize_into(chars, offsets, n_queries, ends[1], ix->d_map, ix->P, st, &Q, S, d_err));
+    FP_TRY(bucketize_into(chars, offsets, n_queries, ends[1], nullptr, 1, ix->d_map, ix->P, st, &Q, S, d_err));
     FilterCfg cfg;
     cfg.mode = FP_MODE_TILED;
     cfg.tq = 256;

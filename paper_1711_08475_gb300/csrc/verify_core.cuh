@@ -1,0 +1,111 @@
+// Device-side verification routines shared by the verification kernels and
+// the fused filter + verify kernel.  See verify.cu for the method.
+#pragma once
+
+#include "common.cuh"
+
+namespace fpk {
+
+// 0x80 in each zero byte of x, 0 elsewhere
+__device__ __forceinline__ uint32_t zero_byte_mask(uint32_t x) {
+    return ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x | 0x7F7F7F7Fu);  // 0x80 in each zero byte
+}
+
+__device__ __forceinline__ bool ham_within(const uint8_t *a, const uint8_t *b, int len, int k) {
+    const uint4 *A = (const uint4 *)a, *B = (const uint4 *)b;
+    int mism = 0;
+    for (int c = 0; c < len; c += 16) {
+        uint4 x = A[c >> 4], y = B[c >> 4];
+        // mismatching bytes = 4 - zero bytes of the XOR (padding is zero on both sides)
+        mism += __popc(~zero_byte_mask(x.x ^ y.x) & 0x80808080u) + __popc(~zero_byte_mask(x.y ^ y.y) & 0x80808080u) +
+                __popc(~zero_byte_mask(x.z ^ y.z) & 0x80808080u) + __popc(~zero_byte_mask(x.w ^ y.w) & 0x80808080u);
+        if (mism > k) return false;
+    }
+    return true;
+}
+
+template <int K>
+__device__ __forceinline__ bool lev_within(const uint8_t *a, int m, const uint8_t *b, int n) {
+    constexpr int BAND = 2 * K + 1;
+    constexpr uint32_t BM = BAND >= 32 ? 0xFFFFFFFFu : ((1u << BAND) - 1u);
+    constexpr int PADW = (K + 3) / 4;  // zero words in front of A so that window offsets are >= 0
+    constexpr int NWIN = (BAND + 3) / 4;
+    constexpr int NREG = ((3 - K + 4 * PADW + 4 * (NWIN - 1)) >> 2) + 2;
+    const uint32_t *A32 = (const uint32_t *)a;
+    const uint32_t *B32 = (const uint32_t *)b;
+    uint32_t R[K + 1];
+#pragma unroll
+    for (int e = 0; e <= K; e++) R[e] = ((((e + 1) >= 32 ? 0xFFFFFFFFu : ((1u << (e + 1)) - 1u))) << K) & BM;
+    uint32_t w[NREG];
+#pragma unroll
+    for (int x = 0; x < NREG; x++) w[x] = x < PADW ? 0u : A32[x - PADW];
+    const int iters = (n + 3) >> 2;
+    for (int it = 0; it < iters; it++) {
+        const uint32_t bw = B32[it];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            if (4 * it + u < n) {
+                const uint32_t tt = ((bw >> (8 * u)) & 0xFFu) * 0x01010101u;
+                uint32_t eq = 0;
+#pragma unroll
+                for (int q = 0; q < NWIN; q++) {
+                    const int off = u - K + 4 * PADW + 4 * q;  // byte offset of the window word
+                    const int wi = off >> 2, sh = (off & 3) * 8;
+                    const uint32_t win = sh ? __funnelshift_r(w[wi], w[wi + 1], sh) : w[wi];
+                    const uint32_t z = zero_byte_mask(win ^ tt) >> 7;  // bits 0, 8, 16, 24
+                    eq |= ((z * 0x00204081u) >> 21 & 0xFu) << (4 * q);
+                }
+                eq &= BM;
+                uint32_t prev = R[0];
+                uint32_t cur = prev & eq;
+                R[0] = cur;
+#pragma unroll
+                for (int e = 1; e <= K; e++) {
+                    const uint32_t old = R[e];
+                    const uint32_t nv = ((old & eq) | prev | (prev >> 1) | (cur << 1)) & BM;
+                    prev = old;
+                    cur = nv;
+                    R[e] = nv;
+                }
+            }
+        }
+        if (R[K] == 0u) return false;
+#pragma unroll
+        for (int x = 0; x + 1 < NREG; x++) w[x] = w[x + 1];
+        const int nx = it + NREG - PADW;
+        w[NREG - 1] = nx < 0 ? 0u : A32[nx];
+    }
+    return (R[K] >> (m - n + K)) & 1u;
+}
+
+// Each banded test compiled once per translation unit, out of line, so that
+// kernels calling it for a runtime k do not carry sixteen inlined copies.
+template <int K>
+static __device__ __noinline__ bool lev_within_outline(const uint8_t *a, int m, const uint8_t *b, int n) {
+    return lev_within<K>(a, m, b, n);
+}
+
+// Lev(a, b) <= k for a runtime k in 0..15 (warp-uniform in every caller, so
+// the switch does not diverge).
+static __device__ __noinline__ bool lev_within_k(int k, const uint8_t *a, int m, const uint8_t *b, int n) {
+    switch (k) {
+        case 0: return lev_within_outline<0>(a, m, b, n);
+        case 1: return lev_within_outline<1>(a, m, b, n);
+        case 2: return lev_within_outline<2>(a, m, b, n);
+        case 3: return lev_within_outline<3>(a, m, b, n);
+        case 4: return lev_within_outline<4>(a, m, b, n);
+        case 5: return lev_within_outline<5>(a, m, b, n);
+        case 6: return lev_within_outline<6>(a, m, b, n);
+        case 7: return lev_within_outline<7>(a, m, b, n);
+        case 8: return lev_within_outline<8>(a, m, b, n);
+        case 9: return lev_within_outline<9>(a, m, b, n);
+        case 10: return lev_within_outline<10>(a, m, b, n);
+        case 11: return lev_within_outline<11>(a, m, b, n);
+        case 12: return lev_within_outline<12>(a, m, b, n);
+        case 13: return lev_within_outline<13>(a, m, b, n);
+        case 14: return lev_within_outline<14>(a, m, b, n);
+        default: return lev_within_outline<15>(a, m, b, n);
+    }
+}
+
+}  // namespace fpk

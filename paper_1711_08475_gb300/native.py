@@ -29,6 +29,10 @@ class fp_query_opts(ctypes.Structure):
                 ("words_per_thread", ctypes.c_int32), ("variant", ctypes.c_int32)]
 
 
+class fp_batch(ctypes.Structure):
+    _fields_ = [("n_queries", ctypes.c_int64), ("k", ctypes.c_int32), ("metric", ctypes.c_int32)]
+
+
 class fp_stats(ctypes.Structure):
     _fields_ = [("n_queries", ctypes.c_int64), ("pairs", ctypes.c_int64), ("survivors", ctypes.c_int64),
                 ("matches", ctypes.c_int64), ("filter_launches", ctypes.c_int64),
@@ -67,6 +71,11 @@ SIGNATURES = {
                                    ctypes.POINTER(_VP)]),
     "fp_query_noalloc": (ctypes.c_int, [_VP, _VP, _VP, _I64, _I32, _I32, _VP, _VP, _I64, ctypes.POINTER(_I64),
                                         _VP]),
+    "fp_query_batched": (ctypes.c_int, [_VP, _VP, _VP, _I64, _VP, _I32, ctypes.POINTER(fp_query_opts), _VP,
+                                        ctypes.POINTER(_VP)]),
+    "fp_plan_create": (ctypes.c_int, [_VP, _I64, _I64, _I32, ctypes.POINTER(fp_query_opts), ctypes.POINTER(_VP)]),
+    "fp_plan_run": (ctypes.c_int, [_VP, _VP, _VP, _I64, _VP, _I32, _VP, ctypes.POINTER(_VP)]),
+    "fp_plan_free": (None, [_VP]),
     "fp_result_csr": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I32]),
     "fp_result_stats": (ctypes.c_int, [_VP, ctypes.POINTER(fp_stats)]),
     "fp_result_free": (None, [_VP]),

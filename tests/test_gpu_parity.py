@@ -43,7 +43,7 @@ def oracle_survivors(d, q, k, metric, m, t, width, b=2, p=3):
 # ---------------------------------------------------------------------------
 
 
-@pytest.mark.parametrize("mode", ["tiled", "plain"])
+@pytest.mark.parametrize("mode", ["tiled", "plain", "fused"])
 @pytest.mark.parametrize("metric", ["ham", "lev"])
 def test_uniform10k_full(fp, metric, mode):
     w = datagen.uniform10k()
@@ -289,3 +289,104 @@ def test_url2m_full_sampled(fp):
         sampled_check(fp, w.dictionary, w.queries[metric], ix, 1, metric, 60, 3)
     ix2 = fp.fp_build(w.dictionary, fp_type="pos", width=32)
     sampled_check(fp, w.dictionary, w.queries["ham"], ix2, 1, "ham", 60, 4)
+
+
+# ---------------------------------------------------------------------------
+# the fused form (filter and verification in one persistent kernel)
+# ---------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("t,width", [("occ", 32), ("count", 32), ("pos", 32), ("occ", 16), ("occh", 16)])
+def test_fused_form(fp, english_small, t, width):
+    w = english_small
+    ix = fp.fp_build(w.dictionary, fp_type=t, width=width)
+    m = ix.symbol_map()
+    for metric in ("ham", "lev"):
+        if metric == "lev" and t in ("occh", "pos"):
+            continue
+        Q = w.queries[metric]
+        for k in (0, 1, 2, 4, 7):
+            res = fp.fp_query_ex(ix, Q, k=k, metric=metric, mode="fused")
+            rp0, idx0 = oracle.match(w.dictionary, Q, k, metric)
+            assert_same(res, rp0, idx0, f"fused {t}{width} {metric} k={k}")
+            pairs, surv = oracle_survivors(w.dictionary, Q, k, metric, m, t, width)
+            st = res.stats()
+            assert (st["pairs"], st["survivors"], st["matches"]) == (pairs, surv, len(idx0))
+
+
+def test_fused_long_strings_and_edges(fp):
+    w = datagen.url2m(6000, 200)
+    ix = fp.fp_build(w.dictionary, fp_type="occ", width=32)
+    for k in (1, 3, 15):
+        Q = w.queries["lev"]
+        rp0, idx0 = oracle.match(w.dictionary, Q, k, "lev")
+        assert_same(fp.fp_query_ex(ix, Q, k=k, metric="lev", mode="fused"), rp0, idx0, f"fused url k={k}")
+    S = datagen.Strings.from_list
+    d = S([b"", b"a", b"ab", b"ab", b"\x00\xff", b"x" * 255, b"abc", b"ba"])
+    q = S([b"", b"a", b"ab", b"b", b"\x00\x00", b"x" * 255, b"zzz", b"abcd"])
+    ix2 = fp.fp_build(d, fp_type="occ", width=32)
+    for metric in ("ham", "lev"):
+        for k in (0, 1, 2, 15):
+            rp0, idx0 = oracle.match(d, q, k, metric)
+            assert_same(fp.fp_query_ex(ix2, q, k=k, metric=metric, mode="fused"), rp0, idx0, f"fused edge {metric} {k}")
+
+
+# ---------------------------------------------------------------------------
+# batched queries (mixed k and metric in one pass) and captured plans
+# ---------------------------------------------------------------------------
+
+
+def mixed_batches(w, sizes, seed):
+    """Consecutive batches drawn from both query sets with assorted (k, metric)."""
+    parts, spec = [], []
+    r = datagen.randint(datagen.stream_key(seed, "mix"), 2 * len(sizes), 0, 7)
+    for i, n in enumerate(sizes):
+        metric = ("ham", "lev")[int(r[2 * i]) % 2]
+        k = int(r[2 * i + 1]) % 4
+        Q = w.queries[metric]
+        start = (i * 97) % max(1, len(Q) - n)
+        parts.append(Q.subset(np.arange(start, start + n)))
+        spec.append((n, k, metric))
+    return datagen.Strings.concat(parts), spec
+
+
+def check_batched(res, w, Q, spec):
+    rp, idx = res.csr()
+    base = 0
+    for (n, k, metric) in spec:
+        sub = Q.subset(np.arange(base, base + n))
+        rp0, idx0 = oracle.match(w.dictionary, sub, k, metric)
+        got_rp = rp[base:base + n + 1] - rp[base]
+        assert np.array_equal(got_rp, rp0), (n, k, metric)
+        assert np.array_equal(idx[rp[base]:rp[base + n]], idx0), (n, k, metric)
+        base += n
+
+
+def test_batched_mixed(fp, english_small):
+    w = english_small
+    Q, spec = mixed_batches(w, [1, 37, 150, 0, 64, 5, 200, 3], 21)
+    for t, width in (("occ", 32), ("count", 32), ("occ", 16)):
+        ix = fp.fp_build(w.dictionary, fp_type=t, width=width)
+        res = fp.fp_query_batched(ix, Q, batches=spec)
+        check_batched(res, w, Q, spec)
+
+
+def test_plan_graph_replay(fp, english_small):
+    import torch
+    w = english_small
+    ix = fp.fp_build(w.dictionary, fp_type="occ", width=32)
+    Q1, spec1 = mixed_batches(w, [100, 7, 250, 31], 5)
+    Q2, spec2 = mixed_batches(w, [300, 1, 12], 6)
+    plan = fp.Plan(ix, max_queries=1000, max_chars=20000, max_batches=16)
+    launches = []
+    for rep in range(3):  # capture, then two replays of the same shape
+        before = fp.fp_launch_count()
+        check_batched(plan.run(Q1, batches=spec1), w, Q1, spec1)
+        launches.append(fp.fp_launch_count() - before)
+    assert launches[1] == launches[2] > 0
+    check_batched(plan.run(Q2, batches=spec2), w, Q2, spec2)  # another shape: captured again
+    dc, do = torch.from_numpy(Q1.chars).cuda(), torch.from_numpy(Q1.offsets).cuda()
+    check_batched(plan.run(dc, do, batches=spec1), w, Q1, spec1)  # device inputs, replayed
+    # a batch set larger than the plan is rejected
+    with pytest.raises(fp.FpError):
+        plan.run(*mixed_batches(w, [600, 600], 7)[:1], batches=[(600, 1, "ham"), (600, 1, "lev")])
