@@ -376,6 +376,7 @@ int fp_query_ex(fp_index *ix, const uint8_t *chars, const int64_t *offsets, int6
     if (fused) cfg.v = 4;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     init_pool();
+    cudaGetLastError();  // launch checks below must not see an unrelated earlier error
 
     fp_result *res = new fp_result();
     res->n_queries = n_queries;
@@ -523,11 +524,12 @@ int fp_query_ex(fp_index *ix, const uint8_t *chars, const int64_t *offsets, int6
     res->stats.survivors = (int64_t)scal[4];
     if (scal[2] > 0) ix->surv_ratio = std::max(1.0 / 4096.0, (double)scal[4] / (double)scal[2]);
     res->stats.matches = (int64_t)scal[5];
-    cudaEventElapsedTime(&res->stats.ms_prepare, R.ev[0], R.ev[1]);
-    cudaEventElapsedTime(&res->stats.ms_filter, R.ev[1], R.ev[2]);
-    cudaEventElapsedTime(&res->stats.ms_verify, R.ev[2], R.ev[3]);
-    cudaEventElapsedTime(&res->stats.ms_emit, R.ev[3], R.ev[4]);
-    cudaEventElapsedTime(&res->stats.ms_total, R.ev[0], R.ev[5]);
+    if (cudaEventElapsedTime(&res->stats.ms_prepare, R.ev[0], R.ev[1]) != cudaSuccess ||
+        cudaEventElapsedTime(&res->stats.ms_filter, R.ev[1], R.ev[2]) != cudaSuccess ||
+        cudaEventElapsedTime(&res->stats.ms_verify, R.ev[2], R.ev[3]) != cudaSuccess ||
+        cudaEventElapsedTime(&res->stats.ms_emit, R.ev[3], R.ev[4]) != cudaSuccess ||
+        cudaEventElapsedTime(&res->stats.ms_total, R.ev[0], R.ev[5]) != cudaSuccess)
+        cudaGetLastError();
 done:
 #undef CK
 #undef TRY

@@ -94,6 +94,7 @@ int alloc_matches(fp_plan *p, int64_t cap) {
 int enqueue(fp_plan *p, int64_t n, int64_t total, int n_batches, int n_groups) {
     fp_index *ix = p->ix;
     const int nbins = 256 * n_groups;
+    cudaGetLastError();  // launch checks below must not see an unrelated earlier error
     FP_CUDA(cudaEventRecord(p->ev_t0, p->st));
     FP_CUDA(cudaMemsetAsync(p->d_err, 0, sizeof(int32_t), p->st));
     FP_TRY(fill_groups(p->d_batch_start, p->d_batch_group, n_batches, p->d_group, p->st));
@@ -324,10 +325,14 @@ int fp_plan_run(fp_plan *p, const uint8_t *chars, const int64_t *offsets, int64_
             res->stats.survivors = (int64_t)sc[4];
             res->stats.matches = (int64_t)sc[5];
             res->stats.filter_launches = 1;
-            cudaEventElapsedTime(&res->stats.ms_filter, p->ev_f0, p->ev_f1);
-            cudaEventElapsedTime(&res->stats.ms_prepare, p->ev_t0, p->ev_f0);
-            cudaEventElapsedTime(&res->stats.ms_emit, p->ev_f1, p->ev_t1);
-            cudaEventElapsedTime(&res->stats.ms_total, p->ev_t0, p->ev_t1);
+            // stage times from the events the pipeline records (left at 0 if the
+            // runtime cannot time them); a failure here must not linger as the
+            // thread's last error
+            if (cudaEventElapsedTime(&res->stats.ms_filter, p->ev_f0, p->ev_f1) != cudaSuccess ||
+                cudaEventElapsedTime(&res->stats.ms_prepare, p->ev_t0, p->ev_f0) != cudaSuccess ||
+                cudaEventElapsedTime(&res->stats.ms_emit, p->ev_f1, p->ev_t1) != cudaSuccess ||
+                cudaEventElapsedTime(&res->stats.ms_total, p->ev_t0, p->ev_t1) != cudaSuccess)
+                cudaGetLastError();
             break;
         }
         // more matches than the buffer holds: grow it to the exact count (the graph
