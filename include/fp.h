@@ -151,6 +151,77 @@ FP_API int fp_query(fp_index *ix, const uint8_t *chars, const int64_t *offsets, 
 FP_API int fp_query_ex(fp_index *ix, const uint8_t *chars, const int64_t *offsets, int64_t n_queries, int k,
                 int metric, const fp_query_opts *opts, void *cuda_stream, fp_result **out);
 
+/* ---- learned symbol-to-bit map (occurrence fingerprints) ----------------- */
+/* Sec. 3.2 builds a fingerprint through "a mapping c -> q" and Sec. 3 picks
+ * the most frequent symbols.  For occurrence fingerprints Eq. 1 stays valid
+ * for ANY map, also many-to-one (one substitution moves at most one symbol
+ * out of and one into the set of fields a string touches), so a map can be
+ * learned for rejection alone; the result is exact whatever the map.
+ *
+ * fp_sample_pairs: n_samples pairs drawn by the method from the index and
+ * the given patterns (a uniform pattern, then a uniform eligible word: equal
+ * length for Ham, length within k for Lev), with: original pattern and word
+ * indices (int32, -1 when no eligible word exists), passed = the pair passes
+ * Eq. 1 under the index's current map, match = D <= k (Sec. 4 verification),
+ * masks = the printable symbols (0x20..0x7E, bit c - 0x20) of the pattern
+ * (words 0-1) and of the word (words 2-3).  Outputs all host or all device.
+ *
+ * Model (FP32, project kernels): per printable symbol c, one-hot input ->
+ * 64 ReLU units -> `fields` logits z_c; A_c = softmax(z_c / tau).  Soft
+ * occurrence fingerprint s_b(S) = 1 - prod_{c in S} (1 - A_c,b); soft
+ * F_D = sum_b s_b(P) + s_b(W) - 2 s_b(P) s_b(W) (equal to F_D for one-hot
+ * A); loss = mean over non-matching samples of softplus(beta (2k+1 - F))/beta.
+ * Parameters (fp_mlp_param_count() floats): W1[64][95], b1[64], W2[32][64],
+ * b2[32] (rows past `fields` unused).
+ *
+ * fp_mlp_loss_grad: one forward + backward on the GPU: *loss_sum = summed
+ * loss, *n_used = non-matching samples, grad = mean gradient.  params, masks,
+ * match, grad: host or device.
+ *
+ * fp_learn_map: Adam over epochs of mini-batches, tau annealed geometrically
+ * from tau0 to tau1; map_out[256] (host) = argmax field per printable symbol,
+ * -1 elsewhere; params_out (optional, host or device) = trained parameters;
+ * loss_curve (optional, host) = mean loss per epoch.  Apply the map with
+ * fp_set_symbol_map. */
+typedef struct {
+    int32_t epochs;  /* 0 = 12 */
+    int32_t batch;   /* samples per step; 0 = 65536 */
+    float lr;        /* 0 = 0.02 */
+    float tau0;      /* 0 = 1.0 */
+    float tau1;      /* 0 = 0.1 */
+    float beta;      /* 0 = 2.0 */
+    uint64_t seed;   /* 0 = 1711 */
+} fp_learn_opts;
+FP_API int fp_mlp_param_count(void);
+FP_API int fp_sample_pairs(fp_index *ix, const uint8_t *chars, const int64_t *offsets, int64_t n_queries, int k,
+                           int metric, int64_t n_samples, uint64_t seed, void *cuda_stream, int32_t *out_q,
+                           int32_t *out_w, uint8_t *out_passed, uint8_t *out_match, uint64_t *out_masks);
+FP_API int fp_mlp_loss_grad(const float *params, int fields, float tau, float beta, int k, const uint64_t *masks,
+                            const uint8_t *match, int64_t n_samples, void *cuda_stream, double *loss_sum,
+                            int64_t *n_used, float *grad);
+FP_API int fp_learn_map(int fields, const uint64_t *masks, const uint8_t *match, int64_t n_samples, int k,
+                        const fp_learn_opts *opts, void *cuda_stream, float *params_out, int8_t *map_out,
+                        float *loss_curve);
+
+/* ---- autotuner ----------------------------------------------------------- */
+/* No paper counterpart.  Times every tile shape (queries per block 32..256,
+ * 4 or 8 fingerprints per thread; for k = 1 also the population-count-only
+ * variant) on the given sample of patterns, `reps` timed runs each after one
+ * warm-up, using the library's stage events (filter + verification time),
+ * and returns the fastest in *best (all candidates in all[0 .. *n_all) when
+ * all is given).  Every candidate's match lists must equal the first one's,
+ * else FP_E_CUDA.  mode: FP_MODE_TILED or FP_MODE_FUSED. */
+typedef struct {
+    int32_t tile_queries;
+    int32_t words_per_thread;
+    int32_t variant;
+    int32_t mode;
+    float ms;
+} fp_tune_result;
+FP_API int fp_autotune(fp_index *ix, const uint8_t *chars, const int64_t *offsets, int64_t n_queries, int k, int metric,
+                       int mode, int reps, void *cuda_stream, fp_tune_result *best, fp_tune_result *all,
+                       int32_t max_all, int32_t *n_all);
+
 /* ---- batched queries and captured plans --------------------------------- */
 /* The paper answers one pattern at a time (Sec. 4: the query fingerprint is
  * built once and compared with every word).  These entry points answer many

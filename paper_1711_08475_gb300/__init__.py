@@ -272,3 +272,69 @@ def fp_probe(kind: int, iters: int = 2000, stream=None) -> dict:
     r = native.fp_probe_result()
     check(load().fp_probe(kind, iters, _stream(stream), ctypes.byref(r)), "fp_probe")
     return r.as_dict()
+
+
+def fp_autotune(index: Index, chars, offsets=None, k: int = 1, metric: str = "ham", mode: str = "tiled",
+                reps: int = 2, stream=None):
+    """Times every tile shape on a pattern sample (fp_autotune); returns (best, all)."""
+    L = load()
+    chars, offsets, n = _strings(chars, offsets)
+    best = native.fp_tune_result()
+    allr = (native.fp_tune_result * 32)()
+    cnt = ctypes.c_int32(0)
+    cp, k1 = _ptr(chars)
+    op, k2 = _ptr(offsets)
+    check(L.fp_autotune(index._h, cp, op, n, k, METRICS[metric], MODES[mode], reps, _stream(stream),
+                        ctypes.byref(best), ctypes.cast(allr, ctypes.c_void_p), 32, ctypes.byref(cnt)), "fp_autotune")
+    return best.as_dict(), [allr[i].as_dict() for i in range(cnt.value)]
+
+
+def fp_sample_pairs(index: Index, chars, offsets=None, k: int = 1, metric: str = "lev", n_samples: int = 100000,
+                    seed: int = 1711, stream=None) -> dict:
+    """Method-generated (pattern, word, passed, match, symbol masks) samples (fp_sample_pairs)."""
+    L = load()
+    chars, offsets, n = _strings(chars, offsets)
+    out = {"q": np.zeros(n_samples, np.int32), "w": np.zeros(n_samples, np.int32),
+           "passed": np.zeros(n_samples, np.uint8), "match": np.zeros(n_samples, np.uint8),
+           "masks": np.zeros((n_samples, 4), np.uint64)}
+    cp, k1 = _ptr(chars)
+    op, k2 = _ptr(offsets)
+    check(L.fp_sample_pairs(index._h, cp, op, n, k, METRICS[metric], n_samples, seed, _stream(stream),
+                            out["q"].ctypes.data, out["w"].ctypes.data, out["passed"].ctypes.data,
+                            out["match"].ctypes.data, out["masks"].ctypes.data), "fp_sample_pairs")
+    return out
+
+
+def fp_mlp_param_count() -> int:
+    return int(load().fp_mlp_param_count())
+
+
+def fp_mlp_loss_grad(params, fields: int, tau: float, beta: float, k: int, masks, match, stream=None):
+    """One GPU forward + backward: (summed loss, non-matching samples, mean gradient)."""
+    L = load()
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    m = np.ascontiguousarray(masks, dtype=np.uint64)
+    mt = np.ascontiguousarray(match, dtype=np.uint8)
+    g = np.zeros(fp_mlp_param_count(), np.float32)
+    loss = ctypes.c_double(0.0)
+    used = ctypes.c_int64(0)
+    check(L.fp_mlp_loss_grad(p.ctypes.data, fields, tau, beta, k, m.ctypes.data, mt.ctypes.data, len(mt),
+                             _stream(stream), ctypes.byref(loss), ctypes.byref(used), g.ctypes.data),
+          "fp_mlp_loss_grad")
+    return loss.value, used.value, g
+
+
+def fp_learn_map(fields: int, masks, match, k: int = 1, epochs: int = 0, batch: int = 0, lr: float = 0.0,
+                 tau0: float = 0.0, tau1: float = 0.0, beta: float = 0.0, seed: int = 0, stream=None):
+    """Trains the map on the GPU: (map int8[256], params float32, loss per epoch)."""
+    L = load()
+    o = native.fp_learn_opts()
+    o.epochs, o.batch, o.lr, o.tau0, o.tau1, o.beta, o.seed = epochs, batch, lr, tau0, tau1, beta, seed
+    m = np.ascontiguousarray(masks, dtype=np.uint64)
+    mt = np.ascontiguousarray(match, dtype=np.uint8)
+    mp = np.zeros(256, np.int8)
+    params = np.zeros(fp_mlp_param_count(), np.float32)
+    curve = np.zeros(max(epochs, 12) if epochs else 12, np.float32)
+    check(L.fp_learn_map(fields, m.ctypes.data, mt.ctypes.data, len(mt), k, ctypes.byref(o), _stream(stream),
+                         params.ctypes.data, mp.ctypes.data, curve.ctypes.data), "fp_learn_map")
+    return mp, params, curve[: (epochs or 12)]

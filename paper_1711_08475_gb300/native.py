@@ -29,6 +29,20 @@ class fp_query_opts(ctypes.Structure):
                 ("words_per_thread", ctypes.c_int32), ("variant", ctypes.c_int32)]
 
 
+class fp_learn_opts(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("tau0", ctypes.c_float), ("tau1", ctypes.c_float), ("beta", ctypes.c_float),
+                ("seed", ctypes.c_uint64)]
+
+
+class fp_tune_result(ctypes.Structure):
+    _fields_ = [("tile_queries", ctypes.c_int32), ("words_per_thread", ctypes.c_int32), ("variant", ctypes.c_int32),
+                ("mode", ctypes.c_int32), ("ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
 class fp_batch(ctypes.Structure):
     _fields_ = [("n_queries", ctypes.c_int64), ("k", ctypes.c_int32), ("metric", ctypes.c_int32)]
 
@@ -76,6 +90,14 @@ SIGNATURES = {
     "fp_plan_create": (ctypes.c_int, [_VP, _I64, _I64, _I32, ctypes.POINTER(fp_query_opts), ctypes.POINTER(_VP)]),
     "fp_plan_run": (ctypes.c_int, [_VP, _VP, _VP, _I64, _VP, _I32, _VP, ctypes.POINTER(_VP)]),
     "fp_plan_free": (None, [_VP]),
+    "fp_mlp_param_count": (ctypes.c_int, []),
+    "fp_sample_pairs": (ctypes.c_int, [_VP, _VP, _VP, _I64, _I32, _I32, _I64, ctypes.c_uint64, _VP, _VP, _VP, _VP,
+                                       _VP, _VP]),
+    "fp_mlp_loss_grad": (ctypes.c_int, [_VP, _I32, ctypes.c_float, ctypes.c_float, _I32, _VP, _VP, _I64, _VP,
+                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64), _VP]),
+    "fp_learn_map": (ctypes.c_int, [_I32, _VP, _VP, _I64, _I32, ctypes.POINTER(fp_learn_opts), _VP, _VP, _VP, _VP]),
+    "fp_autotune": (ctypes.c_int, [_VP, _VP, _VP, _I64, _I32, _I32, _I32, _I32, _VP, _VP, _VP, _I32,
+                                   ctypes.POINTER(ctypes.c_int32)]),
     "fp_result_csr": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I32]),
     "fp_result_stats": (ctypes.c_int, [_VP, ctypes.POINTER(fp_stats)]),
     "fp_result_free": (None, [_VP]),

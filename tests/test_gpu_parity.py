@@ -390,3 +390,22 @@ def test_plan_graph_replay(fp, english_small):
     # a batch set larger than the plan is rejected
     with pytest.raises(fp.FpError):
         plan.run(*mixed_batches(w, [600, 600], 7)[:1], batches=[(600, 1, "ham"), (600, 1, "lev")])
+
+
+def test_autotuner(fp, english_small, tmp_path, monkeypatch):
+    w = english_small
+    ix = fp.fp_build(w.dictionary, fp_type="count", width=32)
+    best, allr = fp.fp_autotune(ix, w.queries["lev"], k=1, metric="lev", mode="tiled", reps=1)
+    assert len(allr) == 16 and best["ms"] == min(r["ms"] for r in allr)
+    assert best["tile_queries"] in (32, 64, 128, 256) and best["words_per_thread"] in (4, 8)
+    best_f, allf = fp.fp_autotune(ix, w.queries["ham"], k=2, metric="ham", mode="fused", reps=1)
+    assert len(allf) == 4 and all(r["words_per_thread"] == 4 for r in allf)
+    from paper_1711_08475_gb300 import tune
+    monkeypatch.setenv("FPMATCH_TUNE_CACHE", str(tmp_path / "tune.json"))
+    o1 = tune.tuned_opts(ix, w.queries["lev"], k=1, metric="lev")
+    o2 = tune.tuned_opts(ix, w.queries["lev"], k=1, metric="lev")  # from the cache
+    assert o1 == o2 and (tmp_path / "tune.json").exists()
+    rp0, idx0 = oracle.match(w.dictionary, w.queries["lev"], 1, "lev")
+    res = fp.fp_query_ex(ix, w.queries["lev"], k=1, metric="lev", tile_queries=o1["tile_queries"],
+                         words_per_thread=o1["words_per_thread"], variant=o1["variant"])
+    assert_same(res, rp0, idx0, "tuned shape")
