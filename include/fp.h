@@ -168,9 +168,11 @@ FP_API int fp_query_ex(fp_index *ix, const uint8_t *chars, const int64_t *offset
  *
  * Model (FP32, project kernels): per printable symbol c, one-hot input ->
  * 64 ReLU units -> `fields` logits z_c; A_c = softmax(z_c / tau).  Soft
- * occurrence fingerprint s_b(S) = 1 - prod_{c in S} (1 - A_c,b); soft
- * F_D = sum_b s_b(P) + s_b(W) - 2 s_b(P) s_b(W) (equal to F_D for one-hot
- * A); loss = mean over non-matching samples of softplus(beta (2k+1 - F))/beta.
+ * F_D = expected Hamming weight of the XOR when symbol c lands on field b
+ * with probability A_c,b: sum_b prod_{c in P&W}(1 - A_c,b) (p_b + q_b -
+ * 2 p_b q_b), p_b (q_b) = 1 - prod over the symbols only in the pattern
+ * (word) of (1 - A_c,b); equal to F_D for one-hot A.  Loss = mean over
+ * non-matching samples of softplus(beta (2k+1 - F))/beta.
  * Parameters (fp_mlp_param_count() floats): W1[64][95], b1[64], W2[32][64],
  * b2[32] (rows past `fields` unused).
  *
@@ -186,7 +188,7 @@ FP_API int fp_query_ex(fp_index *ix, const uint8_t *chars, const int64_t *offset
 typedef struct {
     int32_t epochs;  /* 0 = 12 */
     int32_t batch;   /* samples per step; 0 = 65536 */
-    float lr;        /* 0 = 0.02 */
+    float lr;        /* 0 = 3e-3 */
     float tau0;      /* 0 = 1.0 */
     float tau1;      /* 0 = 0.1 */
     float beta;      /* 0 = 2.0 */

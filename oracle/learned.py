@@ -9,9 +9,13 @@ backward kernels can be checked against it:
   printable symbol c (byte 0x20 + c, c < 95), one-hot input
   h_c  = relu(W1[:, c] + b1)                 W1: 64 x 95, b1: 64
   z_c  = W2[:F] h_c + b2[:F]                 W2: 32 x 64, b2: 32 (first F rows used)
-  A_c  = softmax(z_c / tau)
-  s(S) = 1 - prod_{c in S} (1 - A_c)         soft occurrence fingerprint of symbol set S
-  F_D  = sum_b s_b(P) + s_b(W) - 2 s_b(P) s_b(W)
+  A_c  = softmax(z_c / tau)                  symbol c lands on field b with probability A_c,b
+  F_D  = expected Hamming weight of the XOR of the two occurrence fingerprints
+         (Sec. 3.3) when every symbol lands independently.  With I = P & W,
+         P' = P - W, W' = W - P, field b differs iff no symbol of I lands on it
+         and exactly one of P', W' has a symbol landing on it:
+         F_D = sum_b prod_{c in I} (1 - A_c,b) (p_b + q_b - 2 p_b q_b),
+         p_b = 1 - prod_{c in P'} (1 - A_c,b), q_b the same over W'
   loss = mean over non-matching pairs of softplus(beta (2k + 1 - F_D)) / beta
 
 Pins (tests/test_oracle_learned.py): with one-hot assignments the soft F_D is
@@ -54,16 +58,29 @@ def symbols(mask2) -> list:
     return [c for c in range(64) if (lo >> c) & 1] + [64 + c for c in range(31) if (hi >> c) & 1]
 
 
-def soft_fp(A, syms):
+def none_lands(A, syms):
+    """prod_{c in syms} (1 - A_c): per field, the probability that no symbol of syms lands on it."""
     s = np.ones(A.shape[1])
     for c in syms:
         s = s * (1.0 - A[c])
-    return 1.0 - s
+    return s
+
+
+def split(syms_p, syms_w):
+    """(shared, pattern only, word only) symbol lists."""
+    sp, sw = set(syms_p), set(syms_w)
+    return sorted(sp & sw), sorted(sp - sw), sorted(sw - sp)
+
+
+def soft_fd_fields(A, syms_p, syms_w):
+    I, Pd, Wd = split(syms_p, syms_w)
+    nI = none_lands(A, I)
+    p, q = 1.0 - none_lands(A, Pd), 1.0 - none_lands(A, Wd)
+    return nI * (p + q - 2.0 * p * q)
 
 
 def soft_fd(A, syms_p, syms_w) -> float:
-    sp, sw = soft_fp(A, syms_p), soft_fp(A, syms_w)
-    return float((sp + sw - 2.0 * sp * sw).sum())
+    return float(soft_fd_fields(A, syms_p, syms_w).sum())
 
 
 def loss_and_grad(params, fields: int, tau: float, beta: float, k: int, masks, match):
@@ -76,28 +93,21 @@ def loss_and_grad(params, fields: int, tau: float, beta: float, k: int, masks, m
     for i in range(len(match)):
         if match[i]:
             continue
-        P, W = symbols(masks[i][0:2]), symbols(masks[i][2:4])
-        sp, sw = soft_fp(A, P), soft_fp(A, W)
-        F = float((sp + sw - 2.0 * sp * sw).sum())
+        I, Pd, Wd = split(symbols(masks[i][0:2]), symbols(masks[i][2:4]))
+        nI = none_lands(A, I)
+        p, q = 1.0 - none_lands(A, Pd), 1.0 - none_lands(A, Wd)
+        F = float((nI * (p + q - 2.0 * p * q)).sum())
         t = beta * (T - F)
         total += np.logaddexp(0.0, t) / beta  # softplus(t) / beta
         used += 1
         dLdF = -1.0 / (1.0 + np.exp(-t))
-        gP = dLdF * (1.0 - 2.0 * sw)  # dLoss / ds(P)
-        gW = dLdF * (1.0 - 2.0 * sp)
-        # ds_b(S) / dA_c,b = prod over the other symbols of S of (1 - A_c',b)
-        for c in P:
-            others = np.ones(fields)
-            for c2 in P:
-                if c2 != c:
-                    others = others * (1.0 - A[c2])
-            dA[c] += gP * others
-        for c in W:
-            others = np.ones(fields)
-            for c2 in W:
-                if c2 != c:
-                    others = others * (1.0 - A[c2])
-            dA[c] += gW * others
+        # each derivative is a product over the other symbols of the same group
+        for c in I:
+            dA[c] += dLdF * -none_lands(A, [x for x in I if x != c]) * (p + q - 2.0 * p * q)
+        for c in Pd:
+            dA[c] += dLdF * nI * (1.0 - 2.0 * q) * none_lands(A, [x for x in Pd if x != c])
+        for c in Wd:
+            dA[c] += dLdF * nI * (1.0 - 2.0 * p) * none_lands(A, [x for x in Wd if x != c])
     grad = np.zeros(NPARAM)
     if used == 0:
         return total, used, grad

@@ -10,10 +10,16 @@
 //   h_c = ReLU(W1[:, c] + b1)            (64 hidden units; one-hot input)
 //   z_c = W2 h_c + b2                    (one logit per field, F <= 32)
 //   A_c = softmax(z_c / tau)             (soft assignment of c to the fields)
-// Soft occurrence fingerprint of a string with symbol set S (field b is set
-// unless no symbol of S lands on it):  s_b(S) = 1 - prod_{c in S} (1 - A_c,b).
-// Soft F_D of a pair: sum_b s_b(P) + s_b(W) - 2 s_b(P) s_b(W); with one-hot
-// A_c this is exactly the Hamming weight of the XOR of the fingerprints.
+// Soft F_D of a pair (pattern symbols P, word symbols W): the expected
+// Hamming weight of the XOR of the two fingerprints when every symbol c lands
+// on field b with probability A_c,b, independently.  With I = P & W,
+// P' = P \ W, W' = W \ P, bit b differs iff no symbol of I lands on b and
+// exactly one of P', W' has a symbol landing on b:
+//   f_b = prod_{c in I} (1 - A_c,b) * (p_b + q_b - 2 p_b q_b),
+//   p_b = 1 - prod_{c in P'} (1 - A_c,b),  q_b likewise over W',
+// and F = sum_b f_b.  With one-hot A_c this is exactly the Hamming weight of
+// the XOR (Sec. 3.3); for near-identical strings it is near zero, which is
+// where the loss has to act.
 // Loss on non-matching pairs (matches carry no constraint: the bound stays
 // sound for any map):  softplus(beta (2k + 1 - F)) / beta, i.e. a smooth
 // push of F_D to at least 2k + 1, the rejection threshold of Eq. 1.
@@ -198,17 +204,21 @@ __global__ void __launch_bounds__(256) k_loss_grad(const float *__restrict__ log
     const bool on = lane < F;
     for (int64_t s = warp; s < n; s += nwarps) {
         if (match[s]) continue;  // warp-uniform
-        const uint64_t mp0 = masks[4 * s], mp1 = masks[4 * s + 1], mw0 = masks[4 * s + 2], mw1 = masks[4 * s + 3];
-        float lP = 0.f, lW = 0.f;  // log(1 - s_b)
+        const uint64_t p0 = masks[4 * s], p1 = masks[4 * s + 1], w0 = masks[4 * s + 2], w1 = masks[4 * s + 3];
+        // shared symbols I, symbols only in the pattern P', only in the word W'
+        const uint64_t i0 = p0 & w0, i1 = p1 & w1, a0 = p0 & ~w0, a1 = p1 & ~w1, b0 = w0 & ~p0, b1 = w1 & ~p1;
+        float lI = 0.f, lA = 0.f, lB = 0.f;  // sums of log(1 - A_c,b)
         if (on) {
-            for (uint64_t m = mp0; m; m &= m - 1) lP += s_l[(__ffsll(m) - 1) * MAXF + lane];
-            for (uint64_t m = mp1; m; m &= m - 1) lP += s_l[(64 + __ffsll(m) - 1) * MAXF + lane];
-            for (uint64_t m = mw0; m; m &= m - 1) lW += s_l[(__ffsll(m) - 1) * MAXF + lane];
-            for (uint64_t m = mw1; m; m &= m - 1) lW += s_l[(64 + __ffsll(m) - 1) * MAXF + lane];
+            for (uint64_t m = i0; m; m &= m - 1) lI += s_l[(__ffsll(m) - 1) * MAXF + lane];
+            for (uint64_t m = i1; m; m &= m - 1) lI += s_l[(64 + __ffsll(m) - 1) * MAXF + lane];
+            for (uint64_t m = a0; m; m &= m - 1) lA += s_l[(__ffsll(m) - 1) * MAXF + lane];
+            for (uint64_t m = a1; m; m &= m - 1) lA += s_l[(64 + __ffsll(m) - 1) * MAXF + lane];
+            for (uint64_t m = b0; m; m &= m - 1) lB += s_l[(__ffsll(m) - 1) * MAXF + lane];
+            for (uint64_t m = b1; m; m &= m - 1) lB += s_l[(64 + __ffsll(m) - 1) * MAXF + lane];
         }
-        const float eP = expf(lP), eW = expf(lW);  // 1 - s_b
-        const float sP = 1.f - eP, sW = 1.f - eW;
-        float f = on ? sP + sW - 2.f * sP * sW : 0.f;
+        const float nI = expf(lI), p = 1.f - expf(lA), q = 1.f - expf(lB);
+        const float x = p + q - 2.f * p * q;  // one of P', W' lands on b, the other not
+        float f = on ? nI * x : 0.f;           // and no shared symbol does
 #pragma unroll
         for (int o = 16; o; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
         const float t = beta * (T - f);
@@ -219,23 +229,33 @@ __global__ void __launch_bounds__(256) k_loss_grad(const float *__restrict__ log
             atomicAdd(&s_used, 1ull);
         }
         if (on) {
-            // d s_b(S) / d A_c,b = prod over the other symbols of S of (1 - A) = exp(l_S - log(1 - A_c,b))
-            const float gP = dLdF * (1.f - 2.f * sW) * eP, gW = dLdF * (1.f - 2.f * sP) * eW;
-            for (uint64_t m = mp0; m; m &= m - 1) {
+            // dF_b/dA_c,b = [c in I] (-nI x) / (1 - A_c,b) + [c in P'] nI (1 - 2q) (1 - p) / (1 - A_c,b)
+            //             + [c in W'] nI (1 - 2p) (1 - q) / (1 - A_c,b)
+            const float gI = -dLdF * nI * x, gA = dLdF * nI * (1.f - 2.f * q) * (1.f - p),
+                        gB = dLdF * nI * (1.f - 2.f * p) * (1.f - q);
+            for (uint64_t m = i0; m; m &= m - 1) {
                 const int c = __ffsll(m) - 1;
-                atomicAdd(&s_d[c * MAXF + lane], gP * __expf(-s_l[c * MAXF + lane]));
+                atomicAdd(&s_d[c * MAXF + lane], gI * __expf(-s_l[c * MAXF + lane]));
             }
-            for (uint64_t m = mp1; m; m &= m - 1) {
+            for (uint64_t m = i1; m; m &= m - 1) {
                 const int c = 64 + __ffsll(m) - 1;
-                atomicAdd(&s_d[c * MAXF + lane], gP * __expf(-s_l[c * MAXF + lane]));
+                atomicAdd(&s_d[c * MAXF + lane], gI * __expf(-s_l[c * MAXF + lane]));
             }
-            for (uint64_t m = mw0; m; m &= m - 1) {
+            for (uint64_t m = a0; m; m &= m - 1) {
                 const int c = __ffsll(m) - 1;
-                atomicAdd(&s_d[c * MAXF + lane], gW * __expf(-s_l[c * MAXF + lane]));
+                atomicAdd(&s_d[c * MAXF + lane], gA * __expf(-s_l[c * MAXF + lane]));
             }
-            for (uint64_t m = mw1; m; m &= m - 1) {
+            for (uint64_t m = a1; m; m &= m - 1) {
                 const int c = 64 + __ffsll(m) - 1;
-                atomicAdd(&s_d[c * MAXF + lane], gW * __expf(-s_l[c * MAXF + lane]));
+                atomicAdd(&s_d[c * MAXF + lane], gA * __expf(-s_l[c * MAXF + lane]));
+            }
+            for (uint64_t m = b0; m; m &= m - 1) {
+                const int c = __ffsll(m) - 1;
+                atomicAdd(&s_d[c * MAXF + lane], gB * __expf(-s_l[c * MAXF + lane]));
+            }
+            for (uint64_t m = b1; m; m &= m - 1) {
+                const int c = 64 + __ffsll(m) - 1;
+                atomicAdd(&s_d[c * MAXF + lane], gB * __expf(-s_l[c * MAXF + lane]));
             }
         }
     }
@@ -471,7 +491,7 @@ int fp_learn_map(int fields, const uint64_t *masks, const uint8_t *match, int64_
     if (opts) o = *opts;
     if (o.epochs <= 0) o.epochs = 12;
     if (o.batch <= 0) o.batch = 65536;
-    if (o.lr <= 0.f) o.lr = 0.02f;
+    if (o.lr <= 0.f) o.lr = 3e-3f;
     if (o.tau0 <= 0.f) o.tau0 = 1.0f;
     if (o.tau1 <= 0.f) o.tau1 = 0.1f;
     if (o.beta <= 0.f) o.beta = 2.0f;

@@ -73,11 +73,12 @@ def test_learned_map_rejects_more_at_identical_results(fp, url_small):
     w = url_small
     freq = fp.fp_build(w.dictionary, fp_type="occ", width=32)
     s = fp.fp_sample_pairs(freq, w.queries["lev"], k=1, metric="lev", n_samples=400000, seed=7)
-    mp, params, curve = fp.fp_learn_map(32, s["masks"], s["match"], k=1, epochs=8, seed=3)
+    mp, params, curve = fp.fp_learn_map(32, s["masks"], s["match"], k=1, epochs=12, seed=3)
     assert curve[-1] < curve[0]
     assert (mp[0x20:0x7F] >= 0).all() and (mp[:0x20] == -1).all()
     lrn = fp.fp_build(w.dictionary, fp_type="occ", width=32, custom_map=mp)
-    held = datagen.url2m(200000, 2000, seed=99).queries["lev"]  # other seed: held-out patterns
+    # held-out patterns: other mutations of the same dictionary, other random strings
+    held = datagen.make_queries(w.dictionary, w.law, w.seed, "held/lev", 2000, 0.5, "lev")
     r_f = fp.fp_query(freq, held, k=1, metric="lev")
     r_l = fp.fp_query(lrn, held, k=1, metric="lev")
     rp_f, idx_f = r_f.csr()
@@ -85,7 +86,9 @@ def test_learned_map_rejects_more_at_identical_results(fp, url_small):
     assert np.array_equal(rp_f, rp_l) and np.array_equal(idx_f, idx_l)
     sf, sl = r_f.stats(), r_l.stats()
     assert sf["pairs"] == sl["pairs"]
-    assert sl["survivors"] < sf["survivors"], (sl["survivors"], sf["survivors"])
+    assert sf["matches"] >= 1000
+    # the frequency map of Sec. 3 lets about twice as many pairs through on these strings
+    assert sl["survivors"] < 0.7 * sf["survivors"], (sl["survivors"], sf["survivors"])
     sub = held.subset(np.arange(0, 2000, 40))
     rp0, idx0 = oracle.match(w.dictionary, sub, 1, "lev")
     rows = [idx_l[rp_l[i]:rp_l[i + 1]] for i in range(0, 2000, 40)]

@@ -73,3 +73,30 @@ def test_gradient_matches_finite_differences():
     F = 12
     _, _, g12 = learned.loss_and_grad(p, F, tau, beta, k, masks, match)
     assert np.all(g12[learned.P_W2 + F * learned.HID:learned.P_B2] == 0)
+
+
+def test_soft_fd_is_expected_fd_by_enumeration():
+    """Soft F_D is the expectation of the occurrence-fingerprint F_D (Sec. 3.3)
+    over independent random symbol-to-field assignments: enumerate every
+    assignment of a few symbols to a few fields and weight it by its probability."""
+    import itertools
+    fields = 3
+    rng = datagen.uniform(datagen.stream_key(21, "A"), learned.NSYM * fields).reshape(learned.NSYM, fields) + 0.05
+    A = rng / rng.sum(axis=1, keepdims=True)
+    cases = [([0, 1, 2], [1, 2, 3]), ([4], [5]), ([6, 7], [6, 7]), ([8, 9, 10], []), ([11, 12], [13, 12, 14])]
+    for P, W in cases:
+        syms = sorted(set(P) | set(W))
+        exp = 0.0
+        for assign in itertools.product(range(fields), repeat=len(syms)):
+            pr = 1.0
+            for c, b in zip(syms, assign):
+                pr *= A[c, b]
+            at = dict(zip(syms, assign))
+            fp_p = 0
+            for c in set(P):
+                fp_p |= 1 << at[c]
+            fp_w = 0
+            for c in set(W):
+                fp_w |= 1 << at[c]
+            exp += pr * bin(fp_p ^ fp_w).count("1")
+        assert abs(learned.soft_fd(A, P, W) - exp) <= 1e-12, (P, W)
