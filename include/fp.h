@@ -259,6 +259,72 @@ FP_API int fp_plan_run(fp_plan *plan, const uint8_t *chars, const int64_t *offse
                        const fp_batch *batches, int32_t n_batches, void *cuda_stream, fp_result **out);
 FP_API void fp_plan_free(fp_plan *plan);
 
+/* ---- serving loop: continuous batching over a resident dictionary ------- */
+/* The paper answers one pattern at a time (Sec. 4); this server answers
+ * requests (pattern batches, each with its own k and metric) that arrive
+ * while others run.  fp_server_submit copies a request into host memory and
+ * queues it.  A scheduler thread inside the server keeps up to `lanes`
+ * launches in flight, each on its own CUDA stream: whenever a lane is free
+ * it takes the oldest queued requests that fit one launch (max_requests,
+ * max_queries, max_chars, at most 32 distinct (k, metric)) and whose device
+ * footprint fits what is left of memory_budget (oldest first: a request
+ * that does not fit waits, and so do the ones behind it), and runs them as
+ * one batched launch (the pipeline of fp_plan_run) with its buffers in one
+ * stream-ordered allocation of exactly the launch's size, released when the
+ * launch's results are back in host memory.  Launches of different lanes
+ * overlap on the device.  A request's match lists are the same whether it
+ * runs alone or merged with others.
+ * The index must outlive the server and must not be changed
+ * (fp_set_symbol_map) while the server exists.  The functions may be called
+ * from any thread. */
+typedef struct fp_server fp_server;
+typedef struct {
+    int32_t lanes;          /* launches in flight at once; 0 = 4, at most 64 */
+    int32_t max_requests;   /* requests merged into one launch; 0 = 64 */
+    int64_t max_queries;    /* patterns in one launch (and in one request); 0 = 16384 */
+    int64_t max_chars;      /* pattern bytes in one launch; 0 = 128 * max_queries */
+    int64_t memory_budget;  /* device bytes the launches in flight may hold; 0 = a quarter of the free memory */
+    int32_t tile_queries;   /* as fp_query_opts; 0 = 256 */
+    int32_t variant;        /* as fp_query_opts */
+} fp_server_opts;
+typedef struct {
+    int64_t submitted, completed, queries, launches, reruns; /* reruns: launches re-run with a larger match buffer */
+    int64_t pairs, survivors, matches;                       /* summed over finished launches */
+    int32_t max_lanes_busy;          /* most launches seen in flight at once */
+    int32_t max_requests_per_launch; /* most requests merged into one launch */
+    int64_t budget_bytes, peak_bytes, in_use_bytes; /* admitted device bytes: budget, peak, now */
+    double p50_ms, p99_ms, mean_ms, max_ms;  /* submit -> result ready, over completed requests (nearest rank) */
+    double mean_queue_ms;   /* submit -> admission, over admitted requests */
+    double busy_seconds;    /* wall time with at least one launch in flight */
+} fp_server_stats;
+/* opts NULL = defaults.  Errors: FP_E_INVAL, FP_E_NOMEM (budget below one
+ * single-pattern launch, pinned staging), FP_E_CUDA. */
+FP_API int fp_server_create(fp_index *ix, const fp_server_opts *opts, fp_server **out);
+/* chars, offsets: host (copied before the call returns); 1 <= n_queries <=
+ * max_queries, offsets[n] <= max_chars.  Returns at once with the request's
+ * id.  FP_E_INVAL (bad argument, device pointers, request larger than one
+ * launch), FP_E_UNSUPPORTED (Lev on occurrence-halved / position
+ * fingerprints), FP_E_NOMEM (the request alone exceeds the budget). */
+FP_API int fp_server_submit(fp_server *s, const uint8_t *chars, const int64_t *offsets, int64_t n_queries, int k,
+                            int metric, int64_t *request_id);
+/* Waits at most timeout_us for the request; on FP_OK *out owns its match
+ * lists (host memory: fp_result_csr with on_device = 0; stats.ms_total =
+ * latency, stats.matches) and the id is forgotten.  FP_E_TIMEOUT leaves the
+ * request pending (wait again later); another code is the launch's error. */
+FP_API int fp_server_wait(fp_server *s, int64_t request_id, int64_t timeout_us, fp_result **out);
+FP_API int fp_server_stats_get(fp_server *s, fp_server_stats *out);
+/* Arrival-time driver: request r (patterns [sum of earlier sizes, + request_sizes[r])
+ * of chars/offsets, host) is submitted arrival_us[r] microseconds (non-decreasing)
+ * after the call starts, then every request is waited for (timeout_us in
+ * total).  latency_ms (optional, host, [n_requests]) gets each request's
+ * latency; *out the match lists of all patterns in order. */
+FP_API int fp_server_replay(fp_server *s, const uint8_t *chars, const int64_t *offsets, const int64_t *request_sizes,
+                            const int64_t *arrival_us, int64_t n_requests, int k, int metric, int64_t timeout_us,
+                            double *latency_ms, fp_result **out);
+/* Finishes every queued and running request, then frees the server (results
+ * not waited for are dropped). */
+FP_API void fp_server_free(fp_server *s);
+
 /* ---- query without device allocation ------------------------------------ */
 /* The paper has no counterpart to this entry point: it is a deployment aid.
  * Same result as fp_query for small batches, but the call allocates no device

@@ -21,7 +21,7 @@ METRICS = {"ham": FP_HAM, "lev": FP_LEV}
 SETS = {"common": FP_SET_COMMON, "rare": FP_SET_RARE, "mixed": FP_SET_MIXED, "custom": FP_SET_CUSTOM}
 MODES = {"tiled": FP_MODE_TILED, "plain": FP_MODE_PLAIN, "fused": FP_MODE_FUSED}
 
-__all__ = ["fp_build", "fp_query", "fp_query_ex", "Index", "Result", "fp_launch_count", "fp_version",
+__all__ = ["fp_build", "fp_query", "fp_query_ex", "Index", "Result", "Plan", "Server", "fp_launch_count", "fp_version",
            "fp_probe", "FpError", "TYPES", "METRICS", "SETS", "MODES"]
 
 
@@ -251,6 +251,71 @@ class Plan:
     def free(self):
         if self._h:
             load().fp_plan_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching serving loop over a resident index (fp_server_*).
+
+    submit() copies a request and returns its id at once; wait() blocks (with
+    the GIL released) until the request's match lists are ready."""
+
+    def __init__(self, index: Index, lanes: int = 0, max_requests: int = 0, max_queries: int = 0,
+                 max_chars: int = 0, memory_budget: int = 0, tile_queries: int = 0, variant: int = 0):
+        o = native.fp_server_opts()
+        o.lanes, o.max_requests, o.max_queries, o.max_chars = lanes, max_requests, max_queries, max_chars
+        o.memory_budget, o.tile_queries, o.variant = memory_budget, tile_queries, variant
+        h = ctypes.c_void_p()
+        check(load().fp_server_create(index._h, ctypes.byref(o), ctypes.byref(h)), "fp_server_create")
+        self._h = h.value
+        self.index = index
+
+    def submit(self, chars, offsets=None, k: int = 1, metric: str = "lev") -> int:
+        chars, offsets, n = _strings(chars, offsets)
+        cp, k1 = _ptr(chars)
+        op, k2 = _ptr(offsets)
+        rid = ctypes.c_int64()
+        check(load().fp_server_submit(self._h, cp, op, n, k, METRICS[metric], ctypes.byref(rid)), "fp_server_submit")
+        return rid.value
+
+    def wait(self, request_id: int, timeout_s: float = 60.0) -> Result:
+        h = ctypes.c_void_p()
+        rc = load().fp_server_wait(self._h, request_id, int(timeout_s * 1e6), ctypes.byref(h))
+        check(rc, "fp_server_wait")
+        s = native.fp_stats()
+        check(load().fp_result_stats(h.value, ctypes.byref(s)), "fp_result_stats")
+        return Result(h.value, int(s.n_queries))
+
+    def stats(self) -> dict:
+        s = native.fp_server_stats()
+        check(load().fp_server_stats_get(self._h, ctypes.byref(s)), "fp_server_stats_get")
+        return s.as_dict()
+
+    def replay(self, chars, offsets=None, request_sizes=(), arrival_us=(), k: int = 1, metric: str = "lev",
+               timeout_s: float = 600.0):
+        """Submits request r at arrival_us[r] after the call starts, waits for all:
+        (Result over all patterns in order, latency ms per request)."""
+        chars, offsets, n = _strings(chars, offsets)
+        sizes = np.ascontiguousarray(request_sizes, dtype=np.int64)
+        arr = np.ascontiguousarray(arrival_us, dtype=np.int64)
+        lat = np.zeros(len(sizes), np.float64)
+        cp, k1 = _ptr(chars)
+        op, k2 = _ptr(offsets)
+        h = ctypes.c_void_p()
+        check(load().fp_server_replay(self._h, cp, op, sizes.ctypes.data, arr.ctypes.data, len(sizes), k,
+                                      METRICS[metric], int(timeout_s * 1e6), lat.ctypes.data, ctypes.byref(h)),
+              "fp_server_replay")
+        return Result(h.value, int(sizes.sum())), lat
+
+    def free(self):
+        if self._h:
+            load().fp_server_free(self._h)
             self._h = None
 
     def __del__(self):

@@ -552,6 +552,7 @@ int fp_query(fp_index *ix, const uint8_t *chars, const int64_t *offsets, int64_t
 int fp_result_csr(fp_result *r, const int64_t **row_ptr, const int32_t **idx, int on_device) {
     if (!r || !row_ptr || !idx) return fail(FP_E_INVAL, "null argument");
     if (on_device) {
+        if (!r->d_row_ptr) return fail(FP_E_INVAL, "this result is held in host memory only");
         *row_ptr = r->d_row_ptr;
         *idx = r->d_idx;
         return FP_OK;

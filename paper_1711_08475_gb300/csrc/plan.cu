@@ -17,100 +17,158 @@
 #include <algorithm>
 #include <vector>
 
-#include "common.cuh"
+#include "pipe.cuh"
 
 using namespace fpk;
 
 struct fp_plan {
     fp_index *ix = nullptr;
-    int64_t max_queries = 0, max_chars = 0;
-    int32_t max_batches = 0;
+    PipeShape cap;  // largest run the arena holds (groups = MAX_GROUPS)
     FilterCfg cfg{};
     bool use_graph = true;
     cudaStream_t st = nullptr;
-    cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_f0 = nullptr, ev_f1 = nullptr, ev_t0 = nullptr,
-                ev_t1 = nullptr;
-    // inputs
-    uint8_t *d_chars = nullptr;
-    int64_t *d_off = nullptr;
-    int64_t *d_batch_start = nullptr;  // [max_batches + 1]
-    int32_t *d_batch_group = nullptr;  // [max_batches]
-    int32_t *d_group_km = nullptr;     // [2 * 32]: k then metric per group
-    int32_t *d_group = nullptr;        // [max_queries]
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // start, filter start, filter end, end
+    uint8_t *arena = nullptr;
+    Pipe pipe;
     int64_t *h_batch_start = nullptr;  // pinned staging
     int32_t *h_batch_group = nullptr;
     int32_t *h_group_km = nullptr;
-    // bucketed patterns and scratch
-    Bucketed Q;
-    BucketScratch S{};
-    QueryPlan qp;
-    int32_t *d_err = nullptr;
-    // matches and output
-    int64_t match_cap = 0;
-    uint64_t *matches = nullptr, *tmp = nullptr;
-    uint32_t *radix_hist = nullptr;
-    int64_t *row_ptr = nullptr;
-    int32_t *idx = nullptr;
     uint64_t *h_scal = nullptr;  // pinned: counters + error flag
     // captured graph and its shape
     cudaGraphExec_t exec = nullptr;
     int64_t shape[4] = {-1, -1, -1, -1};
     int64_t kernels_per_run = 0;
-    std::vector<void *> dev_allocs;
 };
+
+namespace fpk {
+
+namespace {
+size_t carve(size_t &off, size_t bytes) {
+    const size_t at = off;
+    off += (bytes + 255) & ~(size_t)255;
+    return at;
+}
+}  // namespace
+
+size_t pipe_layout(const PipeShape &s, uint8_t *base, Pipe *p) {
+    const int64_t nbins = 256 * (int64_t)s.groups;
+    const int64_t n = std::max<int64_t>(s.queries, 1);
+    const int64_t slots = n + (int64_t)(SLOT_ALIGN - 1) * nbins;
+    const int64_t strb = s.chars + 15 * n + STR_SLACK;
+    const int64_t cap = std::max<int64_t>(s.match_cap, 1);
+    const int64_t rh = 256 * (int64_t)std::max(radix_blocks(cap), radix_blocks(n));
+    size_t off = 0;
+    const size_t o_chars = carve(off, (size_t)s.chars + 16), o_off = carve(off, 8 * (size_t)(n + 1)),
+                 o_bs = carve(off, 8 * (size_t)(s.batches + 1)), o_bg = carve(off, 4 * (size_t)s.batches),
+                 o_km = carve(off, 4 * 2 * MAX_GROUPS), o_grp = carve(off, 4 * (size_t)n),
+                 o_qfp = carve(off, 4 * (size_t)(slots + FP_SLACK_SLOTS)), o_qidx = carve(off, 4 * (size_t)slots),
+                 o_qlen = carve(off, (size_t)slots), o_qrow = carve(off, 4 * (size_t)slots),
+                 o_qstr = carve(off, (size_t)strb), o_bst = carve(off, 4 * (size_t)nbins),
+                 o_bct = carve(off, 4 * (size_t)nbins), o_k1 = carve(off, 8 * (size_t)n),
+                 o_k2 = carve(off, 8 * (size_t)n), o_hist = carve(off, 4 * (size_t)nbins),
+                 o_ust = carve(off, 4 * (size_t)nbins), o_s16 = carve(off, 8 * (size_t)nbins),
+                 o_tot = carve(off, 16), o_seg = carve(off, sizeof(Segment) * (size_t)nbins * 31),
+                 o_scal = carve(off, 8 * 8), o_err = carve(off, 4), o_row = carve(off, 8 * (size_t)(n + 1)),
+                 o_m = carve(off, 8 * (size_t)cap), o_t = carve(off, 8 * (size_t)cap),
+                 o_idx = carve(off, 4 * (size_t)cap), o_rh = carve(off, 4 * (size_t)rh);
+    if (base && p) {
+        p->d_chars = base + o_chars;
+        p->d_off = (int64_t *)(base + o_off);
+        p->d_batch_start = (int64_t *)(base + o_bs);
+        p->d_batch_group = (int32_t *)(base + o_bg);
+        p->d_group_km = (int32_t *)(base + o_km);
+        p->d_group = (int32_t *)(base + o_grp);
+        p->Q = Bucketed{};
+        p->Q.fp = base + o_qfp;
+        p->Q.idx = (int32_t *)(base + o_qidx);
+        p->Q.len = base + o_qlen;
+        p->Q.row16 = (uint32_t *)(base + o_qrow);
+        p->Q.str = base + o_qstr;
+        p->Q.b_start = (int32_t *)(base + o_bst);
+        p->Q.b_count = (int32_t *)(base + o_bct);
+        p->S.keys = (uint64_t *)(base + o_k1);
+        p->S.keys2 = (uint64_t *)(base + o_k2);
+        p->S.hist = (int32_t *)(base + o_hist);
+        p->S.ustart = (int32_t *)(base + o_ust);
+        p->S.str16 = (int64_t *)(base + o_s16);
+        p->S.tot = (int64_t *)(base + o_tot);
+        p->S.radix_hist = (uint32_t *)(base + o_rh);
+        p->qp.seg = (Segment *)(base + o_seg);
+        p->qp.scal = (uint64_t *)(base + o_scal);
+        p->d_err = (int32_t *)(base + o_err);
+        p->row_ptr = (int64_t *)(base + o_row);
+        p->match_cap = cap;
+        p->matches = (uint64_t *)(base + o_m);
+        p->tmp = (uint64_t *)(base + o_t);
+        p->idx = (int32_t *)(base + o_idx);
+    }
+    return off;
+}
+
+int group_batches(const fp_index *ix, const fp_batch *batches, int n_batches, int64_t n_queries,
+                  int64_t *batch_start, int32_t *batch_group, int32_t *group_km, int *n_groups) {
+    int ng = 0;
+    int64_t start = 0;
+    for (int b = 0; b < n_batches; b++) {
+        const fp_batch &B = batches[b];
+        if (B.n_queries < 0 || B.k < 0 || B.k > 15 || (B.metric != FP_HAM && B.metric != FP_LEV))
+            return fail(FP_E_INVAL, "bad batch (n_queries, k in 0..15, metric)");
+        if (B.metric == FP_LEV && (ix->P.type == FP_OCC_HALVED || ix->P.type == FP_POS))
+            return fail(FP_E_UNSUPPORTED, "occurrence-halved and position fingerprints bound only the Hamming distance");
+        int g = 0;
+        while (g < ng && !(group_km[g] == B.k && group_km[MAX_GROUPS + g] == B.metric)) g++;
+        if (g == ng) {
+            if (ng == MAX_GROUPS) return fail(FP_E_INVAL, "more than 32 distinct (k, metric) pairs in one run");
+            group_km[g] = B.k;
+            group_km[MAX_GROUPS + g] = B.metric;
+            ng++;
+        }
+        batch_start[b] = start;
+        batch_group[b] = g;
+        start += B.n_queries;
+    }
+    batch_start[n_batches] = start;
+    if (start != n_queries) return fail(FP_E_INVAL, "batch sizes do not add up to n_queries");
+    *n_groups = ng;
+    return FP_OK;
+}
+
+int pipe_enqueue(fp_index *ix, const FilterCfg &cfg, Pipe &p, int64_t n, int64_t total, int n_batches, int n_groups,
+                 cudaStream_t st, uint64_t *h_scal, cudaEvent_t *ev) {
+    const int nbins = 256 * n_groups;
+    cudaGetLastError();  // launch checks below must not see an unrelated earlier error
+    if (ev) FP_CUDA(cudaEventRecord(ev[0], st));
+    FP_CUDA(cudaMemsetAsync(p.d_err, 0, sizeof(int32_t), st));
+    FP_TRY(fill_groups(p.d_batch_start, p.d_batch_group, n_batches, p.d_group, st));
+    FP_TRY(bucketize_into(p.d_chars, p.d_off, n, total, p.d_group, n_groups, ix->d_map, ix->P, st, &p.Q, p.S,
+                          p.d_err));
+    p.qp.max_segments = nbins * 31;
+    FP_TRY(plan_segments(p.Q, ix->D, p.d_group_km, p.d_group_km + MAX_GROUPS, cfg.tq, tile_words(ix->P.width, cfg.v),
+                         &p.qp, st));
+    if (ev) FP_CUDA(cudaEventRecord(ev[1], st));
+    FP_TRY(launch_fused(p.Q, ix->D, p.qp, ix->P, cfg, ix->idx_bits, p.matches, p.match_cap, st, nullptr));
+    if (ev) FP_CUDA(cudaEventRecord(ev[2], st));
+    FP_TRY(build_csr_into(p.matches, p.tmp, p.S.radix_hist, p.qp.scal + 5, p.match_cap, bits_for(n), ix->idx_bits,
+                          n, p.row_ptr, p.idx, st));
+    FP_CUDA(cudaMemcpyAsync(h_scal, p.qp.scal, 8 * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    FP_CUDA(cudaMemcpyAsync(h_scal + 8, p.d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    if (ev) FP_CUDA(cudaEventRecord(ev[3], st));
+    return FP_OK;
+}
+
+}  // namespace fpk
 
 namespace {
 
-constexpr int MAX_GROUPS = 32;
-
-int palloc(fp_plan *p, void **ptr, size_t bytes) {
-    if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(ptr, bytes);
-    if (e != cudaSuccess) return cuda_fail(e, "fp_plan allocation");
-    p->dev_allocs.push_back(*ptr);
-    return FP_OK;
-}
-
-int alloc_matches(fp_plan *p, int64_t cap) {
-    if (p->matches) cudaFree(p->matches);
-    if (p->tmp) cudaFree(p->tmp);
-    if (p->idx) cudaFree(p->idx);
-    if (p->radix_hist) cudaFree(p->radix_hist);
-    p->matches = nullptr;
-    p->tmp = nullptr;
-    p->idx = nullptr;
-    p->radix_hist = nullptr;
-    p->match_cap = cap;
-    const int64_t rh = 256 * (int64_t)std::max(radix_blocks(cap), radix_blocks(p->max_queries));
-    FP_CUDA(cudaMalloc((void **)&p->matches, sizeof(uint64_t) * (size_t)cap));
-    FP_CUDA(cudaMalloc((void **)&p->tmp, sizeof(uint64_t) * (size_t)cap));
-    FP_CUDA(cudaMalloc((void **)&p->idx, sizeof(int32_t) * (size_t)cap));
-    FP_CUDA(cudaMalloc((void **)&p->radix_hist, sizeof(uint32_t) * (size_t)rh));
-    p->S.radix_hist = p->radix_hist;
-    return FP_OK;
-}
-
-// Enqueues the device pipeline on p->st (recorded into a graph when capturing).
-int enqueue(fp_plan *p, int64_t n, int64_t total, int n_batches, int n_groups) {
-    fp_index *ix = p->ix;
-    const int nbins = 256 * n_groups;
-    cudaGetLastError();  // launch checks below must not see an unrelated earlier error
-    FP_CUDA(cudaEventRecord(p->ev_t0, p->st));
-    FP_CUDA(cudaMemsetAsync(p->d_err, 0, sizeof(int32_t), p->st));
-    FP_TRY(fill_groups(p->d_batch_start, p->d_batch_group, n_batches, p->d_group, p->st));
-    FP_TRY(bucketize_into(p->d_chars, p->d_off, n, total, p->d_group, n_groups, ix->d_map, ix->P, p->st, &p->Q, p->S,
-                          p->d_err));
-    p->qp.max_segments = nbins * 31;
-    FP_TRY(plan_segments(p->Q, ix->D, p->d_group_km, p->d_group_km + MAX_GROUPS, p->cfg.tq,
-                         tile_words(ix->P.width, p->cfg.v), &p->qp, p->st));
-    FP_CUDA(cudaEventRecord(p->ev_f0, p->st));
-    FP_TRY(launch_fused(p->Q, ix->D, p->qp, ix->P, p->cfg, ix->idx_bits, p->matches, p->match_cap, p->st, nullptr));
-    FP_CUDA(cudaEventRecord(p->ev_f1, p->st));
-    FP_TRY(build_csr_into(p->matches, p->tmp, p->radix_hist, p->qp.scal + 5, p->match_cap, bits_for(n),
-                          ix->idx_bits, n, p->row_ptr, p->idx, p->st));
-    FP_CUDA(cudaMemcpyAsync(p->h_scal, p->qp.scal, 8 * sizeof(uint64_t), cudaMemcpyDeviceToHost, p->st));
-    FP_CUDA(cudaMemcpyAsync(p->h_scal + 8, p->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, p->st));
-    FP_CUDA(cudaEventRecord(p->ev_t1, p->st));
+// (Re)places the plan's arena for its capacity with `match_cap` matches.
+int plan_arena(fp_plan *p, int64_t match_cap) {
+    if (p->arena) cudaFree(p->arena);
+    p->arena = nullptr;
+    p->cap.match_cap = match_cap;
+    const size_t bytes = pipe_layout(p->cap, nullptr, nullptr);
+    FP_CUDA(cudaMalloc((void **)&p->arena, bytes));
+    pipe_layout(p->cap, p->arena, &p->pipe);
     return FP_OK;
 }
 
@@ -128,84 +186,48 @@ int fp_plan_create(fp_index *ix, int64_t max_queries, int64_t max_chars, int32_t
     if (opts) o = *opts;
     fp_plan *p = new fp_plan();
     p->ix = ix;
-    p->max_queries = max_queries;
-    p->max_chars = max_chars;
-    p->max_batches = max_batches;
+    p->cap.queries = max_queries;
+    p->cap.chars = max_chars;
+    p->cap.batches = max_batches;
+    p->cap.groups = MAX_GROUPS;
     p->cfg.mode = FP_MODE_FUSED;
     p->cfg.v = 4;
     p->cfg.tq = o.tile_queries > 0 ? std::min(o.tile_queries, 256) : 256;
     p->cfg.k1mix = o.variant == 0;  // the kernel takes the mixed test only in k = 1 tiles
     p->use_graph = o.mode != FP_MODE_PLAIN;  // FP_MODE_PLAIN here means: run the pipeline without a graph
-    const int64_t nbins = 256 * MAX_GROUPS;
-    const int64_t slots = max_queries + (int64_t)(SLOT_ALIGN - 1) * nbins;
-    const int64_t strb = max_chars + 15 * max_queries + STR_SLACK;
     int rc = FP_OK;
-#define P_ALLOC(ptr, bytes)                                       \
-    do {                                                          \
-        if ((rc = palloc(p, (void **)&(ptr), (size_t)(bytes))) != FP_OK) goto fail_out; \
-    } while (0)
     if (cudaStreamCreateWithFlags(&p->st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreate(&p->ev_f0) != cudaSuccess || cudaEventCreate(&p->ev_f1) != cudaSuccess ||
-        cudaEventCreate(&p->ev_t0) != cudaSuccess || cudaEventCreate(&p->ev_t1) != cudaSuccess) {
+        cudaEventCreate(&p->ev[0]) != cudaSuccess || cudaEventCreate(&p->ev[1]) != cudaSuccess ||
+        cudaEventCreate(&p->ev[2]) != cudaSuccess || cudaEventCreate(&p->ev[3]) != cudaSuccess) {
         rc = cuda_fail(cudaGetLastError(), "fp_plan_create: stream / events");
-        goto fail_out;
-    }
-    P_ALLOC(p->d_chars, max_chars + 16);
-    P_ALLOC(p->d_off, 8 * (max_queries + 1));
-    P_ALLOC(p->d_batch_start, 8 * (max_batches + 1));
-    P_ALLOC(p->d_batch_group, 4 * max_batches);
-    P_ALLOC(p->d_group_km, 4 * 2 * MAX_GROUPS);
-    P_ALLOC(p->d_group, 4 * max_queries);
-    P_ALLOC(p->Q.fp, 4 * (slots + FP_SLACK_SLOTS));
-    P_ALLOC(p->Q.idx, 4 * slots);
-    P_ALLOC(p->Q.len, slots);
-    P_ALLOC(p->Q.row16, 4 * slots);
-    P_ALLOC(p->Q.str, strb);
-    P_ALLOC(p->Q.b_start, 4 * nbins);
-    P_ALLOC(p->Q.b_count, 4 * nbins);
-    P_ALLOC(p->S.keys, 8 * max_queries);
-    P_ALLOC(p->S.keys2, 8 * max_queries);
-    P_ALLOC(p->S.hist, 4 * nbins);
-    P_ALLOC(p->S.ustart, 4 * nbins);
-    P_ALLOC(p->S.str16, 8 * nbins);
-    P_ALLOC(p->S.tot, 16);
-    P_ALLOC(p->qp.seg, sizeof(Segment) * nbins * 31);
-    P_ALLOC(p->qp.scal, 8 * 8);
-    P_ALLOC(p->d_err, 4);
-    P_ALLOC(p->row_ptr, 8 * (max_queries + 1));
-#undef P_ALLOC
-    if (cudaMallocHost((void **)&p->h_batch_start, 8 * (size_t)(max_batches + 1)) != cudaSuccess ||
-        cudaMallocHost((void **)&p->h_batch_group, 4 * (size_t)max_batches) != cudaSuccess ||
-        cudaMallocHost((void **)&p->h_group_km, 4 * 2 * MAX_GROUPS) != cudaSuccess ||
-        cudaMallocHost((void **)&p->h_scal, 16 * sizeof(uint64_t)) != cudaSuccess) {
+    } else if (cudaMallocHost((void **)&p->h_batch_start, 8 * (size_t)(max_batches + 1)) != cudaSuccess ||
+               cudaMallocHost((void **)&p->h_batch_group, 4 * (size_t)max_batches) != cudaSuccess ||
+               cudaMallocHost((void **)&p->h_group_km, 4 * 2 * MAX_GROUPS) != cudaSuccess ||
+               cudaMallocHost((void **)&p->h_scal, 16 * sizeof(uint64_t)) != cudaSuccess) {
         rc = cuda_fail(cudaErrorMemoryAllocation, "fp_plan_create: pinned staging");
-        goto fail_out;
+    } else {
+        rc = plan_arena(p, std::max<int64_t>(1 << 20, std::min<int64_t>(max_queries * 64, 1LL << 28)));
     }
-    if ((rc = alloc_matches(p, std::max<int64_t>(1 << 20, std::min<int64_t>(max_queries * 64, 1LL << 28)))) != FP_OK)
-        goto fail_out;
+    if (rc != FP_OK) {
+        fp_plan_free(p);
+        return rc;
+    }
     *out = p;
     return FP_OK;
-fail_out:
-    fp_plan_free(p);
-    return rc;
 }
 
 void fp_plan_free(fp_plan *p) {
     if (!p) return;
     if (p->st) cudaStreamSynchronize(p->st);
     if (p->exec) cudaGraphExecDestroy(p->exec);
-    for (void *q : p->dev_allocs) cudaFree(q);
-    if (p->matches) cudaFree(p->matches);
-    if (p->tmp) cudaFree(p->tmp);
-    if (p->idx) cudaFree(p->idx);
-    if (p->radix_hist) cudaFree(p->radix_hist);
+    if (p->arena) cudaFree(p->arena);
     if (p->h_batch_start) cudaFreeHost(p->h_batch_start);
     if (p->h_batch_group) cudaFreeHost(p->h_batch_group);
     if (p->h_group_km) cudaFreeHost(p->h_group_km);
     if (p->h_scal) cudaFreeHost(p->h_scal);
-    cudaEvent_t evs[] = {p->ev_in, p->ev_out, p->ev_f0, p->ev_f1, p->ev_t0, p->ev_t1};
+    cudaEvent_t evs[] = {p->ev_in, p->ev_out, p->ev[0], p->ev[1], p->ev[2], p->ev[3]};
     for (cudaEvent_t e : evs)
         if (e) cudaEventDestroy(e);
     if (p->st) cudaStreamDestroy(p->st);
@@ -216,31 +238,11 @@ int fp_plan_run(fp_plan *p, const uint8_t *chars, const int64_t *offsets, int64_
                 int32_t n_batches, void *cuda_stream, fp_result **out) {
     if (!p || !offsets || !batches || !out || n_queries < 0 || n_batches < 1) return fail(FP_E_INVAL, "fp_plan_run: bad argument");
     *out = nullptr;
-    if (n_queries > p->max_queries || n_batches > p->max_batches)
+    if (n_queries > p->cap.queries || n_batches > p->cap.batches)
         return fail(FP_E_INVAL, "fp_plan_run: more patterns or batches than the plan was made for");
-    fp_index *ix = p->ix;
-    // batches -> groups of equal (k, metric)
     int n_groups = 0;
-    int64_t start = 0;
-    for (int b = 0; b < n_batches; b++) {
-        const fp_batch &B = batches[b];
-        if (B.n_queries < 0 || B.k < 0 || B.k > 15 || (B.metric != FP_HAM && B.metric != FP_LEV))
-            return fail(FP_E_INVAL, "fp_plan_run: bad batch (n_queries, k in 0..15, metric)");
-        if (B.metric == FP_LEV && (ix->P.type == FP_OCC_HALVED || ix->P.type == FP_POS))
-            return fail(FP_E_UNSUPPORTED, "occurrence-halved and position fingerprints bound only the Hamming distance");
-        int g = 0;
-        while (g < n_groups && !(p->h_group_km[g] == B.k && p->h_group_km[MAX_GROUPS + g] == B.metric)) g++;
-        if (g == n_groups) {
-            p->h_group_km[g] = B.k;
-            p->h_group_km[MAX_GROUPS + g] = B.metric;
-            n_groups++;
-        }
-        p->h_batch_start[b] = start;
-        p->h_batch_group[b] = g;
-        start += B.n_queries;
-    }
-    p->h_batch_start[n_batches] = start;
-    if (start != n_queries) return fail(FP_E_INVAL, "fp_plan_run: batch sizes do not add up to n_queries");
+    FP_TRY(group_batches(p->ix, batches, n_batches, n_queries, p->h_batch_start, p->h_batch_group, p->h_group_km,
+                         &n_groups));
     cudaStream_t cs = (cudaStream_t)cuda_stream;
     // inputs into the plan's buffers, ordered after the caller's stream
     int64_t total = 0;
@@ -255,16 +257,17 @@ int fp_plan_run(fp_plan *p, const uint8_t *chars, const int64_t *offsets, int64_
         FP_TRY(check_host_offsets(offsets, n_queries));
         total = offsets[n_queries];
     }
-    if (total > p->max_chars) return fail(FP_E_INVAL, "fp_plan_run: more pattern bytes than the plan was made for");
+    if (total > p->cap.chars) return fail(FP_E_INVAL, "fp_plan_run: more pattern bytes than the plan was made for");
     if (total > 0 && !chars) return fail(FP_E_INVAL, "chars is null");
+    Pipe &P = p->pipe;
     FP_CUDA(cudaEventRecord(p->ev_in, cs));
     FP_CUDA(cudaStreamWaitEvent(p->st, p->ev_in, 0));
-    FP_CUDA(cudaMemcpyAsync(p->d_off, offsets, 8 * (size_t)(n_queries + 1), cudaMemcpyDefault, p->st));
-    if (total > 0) FP_CUDA(cudaMemcpyAsync(p->d_chars, chars, (size_t)total, cudaMemcpyDefault, p->st));
-    FP_CUDA(cudaMemcpyAsync(p->d_batch_start, p->h_batch_start, 8 * (size_t)(n_batches + 1), cudaMemcpyHostToDevice,
+    FP_CUDA(cudaMemcpyAsync(P.d_off, offsets, 8 * (size_t)(n_queries + 1), cudaMemcpyDefault, p->st));
+    if (total > 0) FP_CUDA(cudaMemcpyAsync(P.d_chars, chars, (size_t)total, cudaMemcpyDefault, p->st));
+    FP_CUDA(cudaMemcpyAsync(P.d_batch_start, p->h_batch_start, 8 * (size_t)(n_batches + 1), cudaMemcpyHostToDevice,
                             p->st));
-    FP_CUDA(cudaMemcpyAsync(p->d_batch_group, p->h_batch_group, 4 * (size_t)n_batches, cudaMemcpyHostToDevice, p->st));
-    FP_CUDA(cudaMemcpyAsync(p->d_group_km, p->h_group_km, 4 * 2 * MAX_GROUPS, cudaMemcpyHostToDevice, p->st));
+    FP_CUDA(cudaMemcpyAsync(P.d_batch_group, p->h_batch_group, 4 * (size_t)n_batches, cudaMemcpyHostToDevice, p->st));
+    FP_CUDA(cudaMemcpyAsync(P.d_group_km, p->h_group_km, 4 * 2 * MAX_GROUPS, cudaMemcpyHostToDevice, p->st));
 
     fp_result *res = new fp_result();
     res->n_queries = n_queries;
@@ -284,7 +287,7 @@ int fp_plan_run(fp_plan *p, const uint8_t *chars, const int64_t *offsets, int64_
                 rc = cuda_fail(cudaGetLastError(), "cudaStreamBeginCapture");
                 break;
             }
-            rc = enqueue(p, n_queries, total, n_batches, n_groups);
+            rc = pipe_enqueue(p->ix, p->cfg, P, n_queries, total, n_batches, n_groups, p->st, p->h_scal, p->ev);
             cudaError_t e = cudaStreamEndCapture(p->st, &g);
             if (rc == FP_OK && e != cudaSuccess) rc = cuda_fail(e, "cudaStreamEndCapture");
             if (rc == FP_OK && (e = cudaGraphInstantiate(&p->exec, g, 0)) != cudaSuccess)
@@ -303,7 +306,9 @@ int fp_plan_run(fp_plan *p, const uint8_t *chars, const int64_t *offsets, int64_
             }
             g_launches.fetch_add(p->kernels_per_run);
         } else {
-            if ((rc = enqueue(p, n_queries, total, n_batches, n_groups)) != FP_OK) break;
+            if ((rc = pipe_enqueue(p->ix, p->cfg, P, n_queries, total, n_batches, n_groups, p->st, p->h_scal,
+                                   p->ev)) != FP_OK)
+                break;
         }
         cudaError_t e = cudaStreamSynchronize(p->st);
         if (e != cudaSuccess) {
@@ -319,7 +324,7 @@ int fp_plan_run(fp_plan *p, const uint8_t *chars, const int64_t *offsets, int64_
             rc = fail(FP_E_NOMEM, "tile plan overflow");
             break;
         }
-        if ((int64_t)sc[5] <= p->match_cap) {
+        if ((int64_t)sc[5] <= P.match_cap) {
             res->n_matches = (int64_t)sc[5];
             res->stats.pairs = (int64_t)sc[2];
             res->stats.survivors = (int64_t)sc[4];
@@ -328,15 +333,16 @@ int fp_plan_run(fp_plan *p, const uint8_t *chars, const int64_t *offsets, int64_
             // stage times from the events the pipeline records (left at 0 if the
             // runtime cannot time them); a failure here must not linger as the
             // thread's last error
-            if (cudaEventElapsedTime(&res->stats.ms_filter, p->ev_f0, p->ev_f1) != cudaSuccess ||
-                cudaEventElapsedTime(&res->stats.ms_prepare, p->ev_t0, p->ev_f0) != cudaSuccess ||
-                cudaEventElapsedTime(&res->stats.ms_emit, p->ev_f1, p->ev_t1) != cudaSuccess ||
-                cudaEventElapsedTime(&res->stats.ms_total, p->ev_t0, p->ev_t1) != cudaSuccess)
+            if (cudaEventElapsedTime(&res->stats.ms_filter, p->ev[1], p->ev[2]) != cudaSuccess ||
+                cudaEventElapsedTime(&res->stats.ms_prepare, p->ev[0], p->ev[1]) != cudaSuccess ||
+                cudaEventElapsedTime(&res->stats.ms_emit, p->ev[2], p->ev[3]) != cudaSuccess ||
+                cudaEventElapsedTime(&res->stats.ms_total, p->ev[0], p->ev[3]) != cudaSuccess)
                 cudaGetLastError();
             break;
         }
-        // more matches than the buffer holds: grow it to the exact count (the graph
-        // refers to the old buffers, so it is dropped) and run once more
+        // more matches than the buffer holds: re-place the arena for the exact
+        // count (the graph refers to the old buffers, so it is dropped), copy the
+        // inputs again and run once more
         if (attempt == 1) {
             rc = fail(FP_E_NOMEM, "match buffer sizing failed");
             break;
@@ -346,7 +352,21 @@ int fp_plan_run(fp_plan *p, const uint8_t *chars, const int64_t *offsets, int64_
             p->exec = nullptr;
             p->shape[0] = -1;
         }
-        if ((rc = alloc_matches(p, (int64_t)sc[5])) != FP_OK) break;
+        if ((rc = plan_arena(p, (int64_t)sc[5])) != FP_OK) break;
+        cudaError_t ce;
+        if ((ce = cudaMemcpyAsync(P.d_off, offsets, 8 * (size_t)(n_queries + 1), cudaMemcpyDefault, p->st)) !=
+                cudaSuccess ||
+            (total > 0 && (ce = cudaMemcpyAsync(P.d_chars, chars, (size_t)total, cudaMemcpyDefault, p->st)) !=
+                              cudaSuccess) ||
+            (ce = cudaMemcpyAsync(P.d_batch_start, p->h_batch_start, 8 * (size_t)(n_batches + 1),
+                                  cudaMemcpyHostToDevice, p->st)) != cudaSuccess ||
+            (ce = cudaMemcpyAsync(P.d_batch_group, p->h_batch_group, 4 * (size_t)n_batches, cudaMemcpyHostToDevice,
+                                  p->st)) != cudaSuccess ||
+            (ce = cudaMemcpyAsync(P.d_group_km, p->h_group_km, 4 * 2 * MAX_GROUPS, cudaMemcpyHostToDevice, p->st)) !=
+                cudaSuccess) {
+            rc = cuda_fail(ce, "fp_plan_run: input copy");
+            break;
+        }
     }
     if (rc == FP_OK) {
         // the result owns copies of the plan's output (ordered on the caller's stream)
@@ -356,9 +376,9 @@ int fp_plan_run(fp_plan *p, const uint8_t *chars, const int64_t *offsets, int64_
             (e = cudaMallocAsync((void **)&res->d_row_ptr, 8 * (size_t)(n_queries + 1), cs)) != cudaSuccess ||
             (e = cudaMallocAsync((void **)&res->d_idx, 4 * (size_t)std::max<int64_t>(res->n_matches, 1), cs)) !=
                 cudaSuccess ||
-            (e = cudaMemcpyAsync(res->d_row_ptr, p->row_ptr, 8 * (size_t)(n_queries + 1), cudaMemcpyDeviceToDevice,
+            (e = cudaMemcpyAsync(res->d_row_ptr, P.row_ptr, 8 * (size_t)(n_queries + 1), cudaMemcpyDeviceToDevice,
                                  cs)) != cudaSuccess ||
-            (res->n_matches > 0 && (e = cudaMemcpyAsync(res->d_idx, p->idx, 4 * (size_t)res->n_matches,
+            (res->n_matches > 0 && (e = cudaMemcpyAsync(res->d_idx, P.idx, 4 * (size_t)res->n_matches,
                                                          cudaMemcpyDeviceToDevice, cs)) != cudaSuccess) ||
             (e = cudaStreamSynchronize(cs)) != cudaSuccess)
             rc = cuda_fail(e, "fp_plan_run: result copy");

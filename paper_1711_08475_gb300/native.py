@@ -73,6 +73,25 @@ class fp_probe_result(ctypes.Structure):
         return {n: getattr(self, n) for n, _ in self._fields_}
 
 
+class fp_server_opts(ctypes.Structure):
+    _fields_ = [("lanes", ctypes.c_int32), ("max_requests", ctypes.c_int32), ("max_queries", ctypes.c_int64),
+                ("max_chars", ctypes.c_int64), ("memory_budget", ctypes.c_int64), ("tile_queries", ctypes.c_int32),
+                ("variant", ctypes.c_int32)]
+
+
+class fp_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("queries", ctypes.c_int64),
+                ("launches", ctypes.c_int64), ("reruns", ctypes.c_int64), ("pairs", ctypes.c_int64),
+                ("survivors", ctypes.c_int64), ("matches", ctypes.c_int64), ("max_lanes_busy", ctypes.c_int32),
+                ("max_requests_per_launch", ctypes.c_int32), ("budget_bytes", ctypes.c_int64),
+                ("peak_bytes", ctypes.c_int64), ("in_use_bytes", ctypes.c_int64), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("mean_queue_ms", ctypes.c_double), ("busy_seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
 _VP = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _I32 = ctypes.c_int
@@ -90,6 +109,12 @@ SIGNATURES = {
     "fp_plan_create": (ctypes.c_int, [_VP, _I64, _I64, _I32, ctypes.POINTER(fp_query_opts), ctypes.POINTER(_VP)]),
     "fp_plan_run": (ctypes.c_int, [_VP, _VP, _VP, _I64, _VP, _I32, _VP, ctypes.POINTER(_VP)]),
     "fp_plan_free": (None, [_VP]),
+    "fp_server_create": (ctypes.c_int, [_VP, ctypes.POINTER(fp_server_opts), ctypes.POINTER(_VP)]),
+    "fp_server_submit": (ctypes.c_int, [_VP, _VP, _VP, _I64, _I32, _I32, ctypes.POINTER(_I64)]),
+    "fp_server_wait": (ctypes.c_int, [_VP, _I64, _I64, ctypes.POINTER(_VP)]),
+    "fp_server_stats_get": (ctypes.c_int, [_VP, ctypes.POINTER(fp_server_stats)]),
+    "fp_server_replay": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _I64, _I32, _I32, _I64, _VP, ctypes.POINTER(_VP)]),
+    "fp_server_free": (None, [_VP]),
     "fp_mlp_param_count": (ctypes.c_int, []),
     "fp_sample_pairs": (ctypes.c_int, [_VP, _VP, _VP, _I64, _I32, _I32, _I64, ctypes.c_uint64, _VP, _VP, _VP, _VP,
                                        _VP, _VP]),
