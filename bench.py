@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=12000, help="queries in the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true", help="no CPU leg, no e2e, few steps (for ncu)")
+    ap.add_argument("--url-words", type=int, default=5_000_000, help="URL-like dictionary of the learned/serving legs")
+    ap.add_argument("--url-queries", type=int, default=20_000)
+    ap.add_argument("--serve-seconds", type=float, default=8.0, help="span of the Poisson arrivals")
+    ap.add_argument("--no-url", action="store_true", help="skip the learned-map and serving legs")
     return ap.parse_args()
 
 
@@ -192,6 +196,137 @@ def run_reference(args, w, rank, pg):
             "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def timed(fn, stream, flush, reps: int, warm: int = 2):
+    """Mean device ms of fn() over reps (CUDA events on the launching stream, L2 flushed before each)."""
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    return float(np.mean(ms)), out
+
+
+def same_csr(a, b) -> bool:
+    return np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def url_legs(fp, torch, args, stream, flush):
+    """The learned map and the serving loop on URL-like strings (k = 1, Lev).
+
+    forms: the plain GPU scan (frequency map, one pattern per warp, every
+    dictionary fingerprint read once per pattern) against the batched form
+    (one captured plan: fused filter + verify over all patterns) with the
+    frequency map and with the learned map; every form must give the same
+    match lists, and a sample of patterns is checked against the oracle.
+    serving: Poisson arrivals (mean 5,000 patterns/s, requests of 1..4,096
+    patterns) replayed against the serving loop on the learned index, then the
+    same requests as one burst on the learned and on the frequency index."""
+    import datagen
+    import oracle
+    t0 = time.perf_counter()
+    w, reqs = datagen.serving5m(args.url_words, duration_s=args.serve_seconds)
+    gen_s = time.perf_counter() - t0
+    freq = fp.fp_build(w.dictionary, fp_type="occ", width=32)
+    # training pairs: the frequency-map filter on patterns of their own (not the measured ones)
+    train_q = datagen.make_queries(w.dictionary, w.law, w.seed, "train/lev", 20000, 0.5, "lev")
+    torch.cuda.synchronize()
+    ts = time.perf_counter()
+    smp = fp.fp_sample_pairs(freq, train_q, k=1, metric="lev", n_samples=2_000_000, seed=11)
+    t1 = time.perf_counter()
+    mp, params, curve = fp.fp_learn_map(32, smp["masks"], smp["match"], k=1, seed=3)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    lrn = fp.fp_build(w.dictionary, fp_type="occ", width=32, custom_map=mp)
+    Q = datagen.make_queries(w.dictionary, w.law, w.seed, "bench/lev", args.url_queries, 0.5, "lev")
+    dq = (torch.from_numpy(Q.chars).cuda(), torch.from_numpy(Q.offsets).cuda())
+    nq = len(Q)
+    plans = {name: fp.Plan(ix, nq, len(Q.chars), 1) for name, ix in (("freq", freq), ("learned", lrn))}
+    batch = [(nq, 1, "lev")]
+
+    def plain():
+        return fp.fp_query_ex(freq, dq[0], dq[1], k=1, metric="lev", mode="plain")
+
+    def batched(name):
+        return lambda: plans[name].run(dq[0], dq[1], batches=batch)
+
+    forms = {}
+    outs = {}
+    for name, fn, reps in (("plain_gpu_freq", plain, 3), ("batched_freq", batched("freq"), 5),
+                           ("batched_learned", batched("learned"), 5)):
+        ms, r = timed(fn, stream, flush, reps)
+        st = r.stats()
+        outs[name] = r.csr()
+        r.free()
+        forms[name] = {"queries_per_s": nq / (ms / 1e3), "pair_compares_per_s": st["pairs"] / (ms / 1e3),
+                       "ms": ms, "pairs": st["pairs"], "survivors": st["survivors"], "matches": st["matches"],
+                       "rejection_rate": 1.0 - st["survivors"] / max(st["pairs"], 1)}
+    ref = outs["plain_gpu_freq"]
+    identical = all(same_csr(ref, o) for o in outs.values())
+    pick = np.arange(0, nq, max(1, nq // 48))[:48]
+    orp, oidx = oracle.match(w.dictionary, Q.subset(pick), 1, "lev", threads=os.cpu_count() or 1)
+    rp, idx = outs["batched_learned"]
+    oracle_ok = all(np.array_equal(idx[rp[i]:rp[i + 1]], oidx[orp[j]:orp[j + 1]]) for j, i in enumerate(pick))
+    for p in plans.values():
+        p.free()
+
+    # ---- serving loop ----------------------------------------------------
+    allq = datagen.Strings.concat([r.queries for r in reqs])
+    sizes = np.array([len(r.queries) for r in reqs], np.int64)
+    arrive = np.array([int(r.arrival_s * 1e6) for r in reqs], np.int64)
+    srv = fp.Server(lrn, lanes=4)
+    t0 = time.perf_counter()
+    res, lat = srv.replay(allq, request_sizes=sizes, arrival_us=arrive, k=1, metric="lev")
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.free()
+    served = res.csr()
+    res.free()
+    burst = {}
+    for name, ix in (("learned", lrn), ("freq", freq)):
+        srv = fp.Server(ix, lanes=4)
+        t0 = time.perf_counter()
+        r, blat = srv.replay(allq, request_sizes=sizes, arrival_us=np.zeros_like(arrive), k=1, metric="lev")
+        bw = time.perf_counter() - t0
+        bst = srv.stats()
+        srv.free()
+        burst[name] = {"queries_per_s": len(allq) / bw, "p50_ms": bst["p50_ms"], "p99_ms": bst["p99_ms"],
+                       "launches": bst["launches"], "max_requests_per_launch": bst["max_requests_per_launch"],
+                       "rejection_rate": 1.0 - bst["survivors"] / max(bst["pairs"], 1),
+                       "identical_to_offered_run": same_csr(r.csr(), served)}
+        r.free()
+    return {
+        "forms": {"workload": f"{len(w.dictionary):,} URL-like strings (lognormal lengths median 45, 15..120, 40% "
+                              f"shared prefixes), {nq:,} Lev patterns (50% one-edit mutations), k=1, occ32",
+                  "forms": forms,
+                  "learned_batched_vs_plain_gpu": forms["batched_learned"]["queries_per_s"]
+                                                  / forms["plain_gpu_freq"]["queries_per_s"],
+                  "identical_results": identical,
+                  "oracle_checked_patterns": int(len(pick)), "oracle_ok": oracle_ok,
+                  "learned_map": {"samples": 2_000_000, "sample_s": t1 - ts, "train_s": t2 - t1,
+                                  "loss_first_epoch": float(curve[0]), "loss_last_epoch": float(curve[-1]),
+                                  "fields_used": int(len(set(mp[0x20:0x7F].tolist())))},
+                  "generation_s": gen_s},
+        "serving": {"workload": f"{len(reqs)} requests ({len(allq):,} Lev patterns, sizes U{{1..4096}}) with "
+                                f"Poisson arrivals, mean 5,000 patterns/s over {args.serve_seconds:g} s, k=1, "
+                                f"learned occ32 index, 4 lanes",
+                    "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "max_ms": st["max_ms"],
+                    "mean_queue_ms": st["mean_queue_ms"], "offered_queries_per_s": len(allq) / args.serve_seconds,
+                    "achieved_queries_per_s": len(allq) / wall, "launches": st["launches"],
+                    "max_lanes_busy": st["max_lanes_busy"], "peak_bytes": st["peak_bytes"],
+                    "budget_bytes": st["budget_bytes"],
+                    "rejection_rate": 1.0 - st["survivors"] / max(st["pairs"], 1),
+                    "burst": burst},
+    }
+
+
 def main():
     args = parse()
     import datagen
@@ -287,7 +422,7 @@ def main():
         "config": {"workload": WORKLOAD, "fingerprint": f"{args.fp_type}32", "k": 1, "metrics": list(metrics),
                    "queries_per_step": n_q_step, "dictionary_words": len(w.dictionary),
                    "l2": "flushed between timed steps (256 MB write, outside the timed events)",
-                   "mode": "tiled filter (64 queries x 2048 words per tile), separate verify"},
+                   "mode": "tiled filter (256 queries per tile, 4 fingerprint words per thread), separate verify"},
         "pair_compares_per_s": world * pairs * args.steps / t_dev,
         "pairs_per_step": pairs, "survivors_per_step": surv, "matches_per_step": matches,
         "rejection_rate": 1.0 - surv / pairs if pairs else None,
@@ -328,6 +463,8 @@ def main():
             import oracle
             oracle.build()
             result["cpu_baseline"] = cpu_baseline(w, args.cpu_sample)
+        if not args.no_url and rank == 0:
+            result.update(url_legs(fp, torch, args, stream, flush))
     result["generation_s"] = t_gen
     if rank == 0:
         print(json.dumps(result), flush=True)

@@ -93,10 +93,24 @@ def categorical(key, n: int, weights: np.ndarray, chunk: int = 1 << 24) -> np.nd
     cdf = np.cumsum(np.asarray(weights, dtype=np.float64))
     cdf /= cdf[-1]
     out = np.empty(n, dtype=np.int64)
+    # searchsorted(cdf, u, "right") through a 4096-cell guide table: start at the
+    # count of cdf entries <= the cell's left edge, then step over the few
+    # entries inside the cell (same result as a full binary search, faster)
+    T = 4096
+    guide = np.searchsorted(cdf, np.arange(T, dtype=np.float64) / T, side="right")
+    last = len(cdf) - 1
     for s in range(0, n, chunk):
         e = min(n, s + chunk)
-        out[s:e] = np.searchsorted(cdf, uniform(key, e - s, s), side="right")
-    np.minimum(out, len(cdf) - 1, out=out)
+        u = uniform(key, e - s, s)
+        r = guide[(u * T).astype(np.int64)]
+        while True:
+            step = cdf[np.minimum(r, last)] <= u
+            step &= r <= last
+            if not step.any():
+                break
+            r += step
+        out[s:e] = r
+    np.minimum(out, last, out=out)
     return out
 
 
