@@ -196,6 +196,24 @@ def run_reference(args, w, rank, pg):
             "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def filter_traffic():
+    """DRAM bytes per filter launch from the committed ncu summary, or None once
+    the kernel sources differ from the ones the counters were taken on."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", "filter_tiled_english1m_traffic.md")
+    csrc = os.path.join(ROOT, "paper_1711_08475_gb300", "csrc")
+    if not os.path.exists(prof):
+        return None
+    h = hashlib.sha256()
+    for f in ("filter.cu", "common.cuh", "verify_core.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    kv = dict(line.split(": ", 1) for line in open(prof).read().splitlines()
+              if line.startswith(("source_hash: ", "bytes_per_launch: ")))
+    if kv.get("source_hash") != h.hexdigest()[:16]:
+        return None
+    return int(kv["bytes_per_launch"])
+
+
 def timed(fn, stream, flush, reps: int, warm: int = 2):
     """Mean device ms of fn() over reps (CUDA events on the launching stream, L2 flushed before each)."""
     import torch
@@ -407,13 +425,7 @@ def main():
     mhz = clocks["sm_mhz"] or probe[0]["sm_clock_mhz"]
     peak = sms * mhz * 1e6 * per_clk
     achieved = pairs / (filt_ms / 1e3)
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "filter_traffic.json")
-    if os.path.exists(prof):
-        try:
-            traffic = json.load(open(prof)).get("bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = filter_traffic()
 
     result = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
