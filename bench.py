@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--url-queries", type=int, default=20_000)
     ap.add_argument("--serve-seconds", type=float, default=8.0, help="span of the Poisson arrivals")
     ap.add_argument("--no-url", action="store_true", help="skip the learned-map and serving legs")
+    ap.add_argument("--variant", type=int, default=0, help="filter variant (fp_query_opts.variant)")
     return ap.parse_args()
 
 
@@ -380,7 +381,7 @@ def main():
     def step_device():
         stats = []
         for m in metrics:
-            r = fp.fp_query(ix, dev[m][0], dev[m][1], k=1, metric=m)
+            r = fp.fp_query_ex(ix, dev[m][0], dev[m][1], k=1, metric=m, variant=args.variant)
             stats.append(r.stats())
             r.free()
         return stats
@@ -460,7 +461,8 @@ def main():
             t0 = time.perf_counter()
             got = 0
             for m in metrics:
-                r = fp.fp_query(ix, pinned[m][0].numpy(), pinned[m][1].numpy(), k=1, metric=m)
+                r = fp.fp_query_ex(ix, pinned[m][0].numpy(), pinned[m][1].numpy(), k=1, metric=m,
+                                    variant=args.variant)
                 rp, idx = r.csr()
                 got += rp.nbytes + idx.nbytes
                 r.free()

@@ -94,7 +94,12 @@ typedef struct {
     int32_t tile_queries;    /* queries per block for FP_MODE_TILED / FUSED; 0 = autotuned / default */
     int32_t words_per_thread;/* dictionary fingerprints per thread per tile, 4 or 8; 0 = default */
     int32_t variant;         /* 0 = automatic (k = 1: a quarter of the pair tests use an ALU-only
-                                "at most two bits" test, identical decisions); 1 = population count only */
+                                "at most two bits" test, identical decisions); 1 = population count only;
+                                2 = tensor cores for occ / occh / count fingerprints: with set bits as +1
+                                and clear bits as -1 the dot product of two fingerprints is W - 2 F_D, so
+                                FP8 MMA dot products decide Eq. 1 exactly (128 patterns x 1024 words per
+                                tile; tile_queries and words_per_thread do not apply; position
+                                fingerprints keep the population-count kernel) */
 } fp_query_opts;
 
 typedef struct {

@@ -365,13 +365,14 @@ int fp_query_ex(fp_index *ix, const uint8_t *chars, const int64_t *offsets, int6
     if (opts) o = *opts;
     if (o.mode != FP_MODE_TILED && o.mode != FP_MODE_PLAIN && o.mode != FP_MODE_FUSED)
         return fail(FP_E_UNSUPPORTED, "query mode not available");
-    FilterCfg cfg;
+    FilterCfg cfg{};
     cfg.mode = o.mode;
     // defaults from a sweep on the 1M-word English-like workload: 4 words per
     // thread, 256 queries per tile
     cfg.v = o.words_per_thread == 8 ? 8 : 4;
     cfg.tq = o.mode == FP_MODE_PLAIN ? 1 : (o.tile_queries > 0 ? std::min(o.tile_queries, 256) : 256);
     cfg.k1mix = o.variant == 0 && k == 1;
+    cfg.mma = o.variant == 2 && o.mode != FP_MODE_PLAIN;
     const bool fused = o.mode == FP_MODE_FUSED;
     if (fused) cfg.v = 4;
     cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -399,7 +400,8 @@ int fp_query_ex(fp_index *ix, const uint8_t *chars, const int64_t *offsets, int6
     uint64_t scal[8] = {0};
     int32_t h_err = 0;
     const int q_bits = bits_for(n_queries), idx_bits = ix->idx_bits;
-    const int tw = tile_words(ix->P.width, cfg.v);
+    int tq = 0, tw = 0;
+    tile_shape(cfg, ix->P, &tq, &tw);
     int64_t pairs_bound;
     cudaError_t e;
 #define CK(call)                                 \
@@ -429,7 +431,7 @@ int fp_query_ex(fp_index *ix, const uint8_t *chars, const int64_t *offsets, int6
     R.plan.max_segments = 256 * (2 * k + 1);
     CK(cudaMallocAsync((void **)&R.plan.seg, sizeof(Segment) * (size_t)R.plan.max_segments, st));
     CK(cudaMallocAsync((void **)&R.plan.scal, 8 * sizeof(uint64_t), st));
-    TRY(plan_segments(R.Q, ix->D, R.d_group, R.d_group + 1, cfg.tq, tw, &R.plan, st));
+    TRY(plan_segments(R.Q, ix->D, R.d_group, R.d_group + 1, tq, tw, &R.plan, st));
     // survivor capacity: exact pair count when the host saw the lengths, else a bound
     if (S.host_checked) {
         pairs_bound = host_pairs(ix, S.host_len_hist, k, metric);

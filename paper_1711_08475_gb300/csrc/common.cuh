@@ -130,6 +130,7 @@ struct FilterCfg {
     int tq;        // queries per tile
     int v;         // 32-bit fingerprint words per thread (4 or 8)
     bool k1mix;    // k = 1: test a quarter of the words with integer ALU ops instead of POPC
+    bool mma;      // popcount-type fingerprints: dot products of +-1 vectors on the tensor cores
 };
 
 int plan_segments(const Bucketed &q, const Bucketed &d, const int32_t *d_group_k,
@@ -150,6 +151,8 @@ int launch_verify(const Bucketed &q, const Bucketed &d, const uint64_t *surv, co
                   int64_t surv_cap, int k, int metric, int idx_bits, uint64_t *matches,
                   uint64_t *d_n_matches, int64_t match_cap, cudaStream_t st);
 int tile_words(int width, int v);
+// Tile of the filter kernel the configuration selects: patterns x words.
+void tile_shape(const FilterCfg &cfg, const FpParams &fp, int *tq, int *tw);
 int fingerprint_list(const uint8_t *d_chars, const int64_t *d_off, int64_t n, const int8_t *d_map,
                      const FpParams &P, uint32_t *d_out, cudaStream_t st);
 

@@ -21,6 +21,8 @@
 // queries each thread re-tests just the queries whose bit is set and appends
 // the passing pairs to a per-warp buffer in shared memory.  A full buffer is
 // flushed to the global survivor list with one atomic reservation per flush.
+#include <cuda_fp16.h>
+
 #include "verify_core.cuh"
 
 namespace fpk {
@@ -529,6 +531,167 @@ __global__ void __launch_bounds__(FT_THREADS, FT_MIN_BLOCKS) k_filter_tiled(Filt
     if (!FUSED) flush_stage(A, stage, cnt, lane);
 }
 
+// ---------------------------------------------------------------------------
+// the same filter on the tensor cores
+// ---------------------------------------------------------------------------
+// With bit b of a fingerprint mapped to s_b = +1 (set) or -1 (clear), the dot
+// product of two fingerprints' sign vectors is W - 2 F_D (every equal bit adds
+// one, every differing bit subtracts one; F_D = H_W(x XOR y), Sec. 3.3), so
+// F_D <= 2k (Eq. 1) iff dot >= W - 4k.  One mma.sync.m16n8k32 on FP8 (E4M3)
+// operands, which hold +1 and -1 exactly, gives a warp 16 x 8 such dot
+// products; they are integers of magnitude <= 32, exact in the FP16
+// accumulators.  The accumulator starts at 0.5 - (W - 4k), so a pair passes
+// iff its result is positive, i.e. iff its FP16 sign bit is clear.  A thread
+// ANDs its results together and looks at them one by one only when a sign
+// bit survives; passing pairs go to the same per-warp staging as above.
+//
+// Bit b of the fingerprint is K position (b / 8) * 4 + b % 4 (+16 for
+// b % 8 >= 4) in both operands, which puts the eight bits a thread of the
+// mma layout needs into one byte: thread t of a quad takes byte t, expanded
+// to eight FP8 values by a 256-entry table.  16-bit fingerprints use the
+// first 16 positions and leave the other 16 zero.
+constexpr int FM_TQ = 128;                       // patterns per tile: 8 row tiles of 16
+constexpr int FM_RT = FM_TQ / 16;
+constexpr int FM_GROUPS = 16;                    // groups of 8 words per warp and tile
+constexpr int FM_TW = FT_WARPS * FM_GROUPS * 8;  // 1024 words per tile
+#ifndef FM_MIN_BLOCKS
+#define FM_MIN_BLOCKS 2
+#endif
+
+__device__ __forceinline__ void mma_e4m3_f16(uint32_t &d0, uint32_t &d1, const uint32_t (&a)[4], uint32_t b0,
+                                             uint32_t b1, uint32_t c) {
+    asm("mma.sync.aligned.m16n8k32.row.col.f16.e4m3.e4m3.f16 {%0,%1}, {%2,%3,%4,%5}, {%6,%7}, {%8,%8};"
+        : "=r"(d0), "=r"(d1)
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "r"(c));
+}
+
+template <int W, bool FUSED>
+__global__ void __launch_bounds__(FT_THREADS, FM_MIN_BLOCKS) k_filter_mma(FilterArgs A) {
+    __shared__ uint2 s_lut[256];  // byte -> eight E4M3 values (+1 for a set bit, -1 for a clear one)
+    __shared__ uint32_t s_q[FM_TQ];
+    __shared__ __align__(16) uint32_t s_w[FM_TW];
+    __shared__ uint64_t s_stage[FT_WARPS][FT_STAGE];
+    __shared__ uint32_t s_cnt[FT_WARPS];
+    __shared__ uint64_t s_tile;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    for (int v = threadIdx.x; v < 256; v += FT_THREADS) {
+        uint32_t lo = 0, hi = 0;
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            lo |= (((v >> i) & 1) ? 0x38u : 0xB8u) << (8 * i);
+            hi |= (((v >> (4 + i)) & 1) ? 0x38u : 0xB8u) << (8 * i);
+        }
+        s_lut[v] = make_uint2(lo, hi);
+    }
+    const int nseg = (int)A.scal[0];
+    const uint64_t ntiles = A.scal[1];
+    uint64_t *stage = s_stage[warp];
+    uint32_t *cnt = &s_cnt[warp];
+    if (lane == 0) *cnt = 0;
+    const bool live = W == 32 || t < 2;  // 16-bit fingerprints: bytes 2 and 3 stay zero
+    const uint32_t wrel0 = (uint32_t)warp * (FM_GROUPS * 8);
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd((unsigned long long *)&A.scal[3], 1ull);
+        __syncthreads();
+        const uint64_t tile = s_tile;
+        if (tile >= ntiles) break;
+        const Segment S = A.seg[find_segment(A.seg, nseg, tile)];
+        const uint64_t local = tile - S.tile_begin;
+        const uint32_t qt = (uint32_t)(local / S.n_dtiles), dt = (uint32_t)(local % S.n_dtiles);
+        const uint32_t q0 = S.q_start + qt * (uint32_t)FM_TQ;
+        const uint32_t nq = min((uint32_t)FM_TQ, S.q_count - qt * (uint32_t)FM_TQ);
+        const uint32_t w0 = S.d_start + dt * (uint32_t)FM_TW;
+        const uint32_t nw = min((uint32_t)FM_TW, S.d_count - dt * (uint32_t)FM_TW);
+        for (uint32_t j = threadIdx.x; j < (uint32_t)FM_TQ; j += FT_THREADS)
+            s_q[j] = j < nq ? ((W == 32) ? A.qfp32[q0 + j] : (uint32_t)A.qfp16[q0 + j]) : 0u;
+        if (W == 32) {
+            // w0 is a multiple of 8 slots and the slack after the last bucket is
+            // readable, so whole 128-bit vectors may be loaded past nw
+            for (uint32_t j = threadIdx.x; j * 4 < nw; j += FT_THREADS)
+                *reinterpret_cast<uint4 *>(&s_w[4 * j]) = *reinterpret_cast<const uint4 *>(A.dfp + w0 + 4 * j);
+        } else {
+            const uint16_t *d16 = reinterpret_cast<const uint16_t *>(A.dfp);
+            for (uint32_t j = threadIdx.x; j < nw; j += FT_THREADS) s_w[j] = d16[w0 + j];
+        }
+        __syncthreads();
+        const int nr = (int)((nq + 15u) / 16u);
+        const float Tf = (float)((W == 32 ? 32 : 16) - 4 * S.k);  // pass iff dot >= W - 4k
+        const __half2 hb = __float2half2_rn(0.5f - Tf);
+        const uint32_t bias = *reinterpret_cast<const uint32_t *>(&hb);
+        uint32_t a[FM_RT][4];
+#pragma unroll
+        for (int r = 0; r < FM_RT; r++) {
+            const uint32_t r0 = (uint32_t)(r * 16 + g), r1 = r0 + 8u;
+            uint2 x0 = make_uint2(0u, 0u), x1 = make_uint2(0u, 0u);
+            if (live && r0 < nq) x0 = s_lut[(s_q[r0] >> (8 * t)) & 0xFFu];
+            if (live && r1 < nq) x1 = s_lut[(s_q[r1] >> (8 * t)) & 0xFFu];
+            a[r][0] = x0.x;
+            a[r][1] = x1.x;
+            a[r][2] = x0.y;
+            a[r][3] = x1.y;
+        }
+        for (int gi = 0; gi < FM_GROUPS; gi++) {
+            const uint32_t wrel = wrel0 + (uint32_t)gi * 8u;
+            if (wrel >= nw) break;  // warp-uniform
+            uint32_t b0 = 0u, b1 = 0u;
+            if (live && wrel + g < nw) {
+                const uint2 x = s_lut[(s_w[wrel + g] >> (8 * t)) & 0xFFu];
+                b0 = x.x;
+                b1 = x.y;
+            }
+            uint32_t d[FM_RT][2];
+            uint32_t all = 0xFFFFFFFFu;
+#pragma unroll
+            for (int r = 0; r < FM_RT; r++) {
+                if (r < nr) {
+                    mma_e4m3_f16(d[r][0], d[r][1], a[r], b0, b1, bias);
+                    all &= d[r][0] & d[r][1];
+                } else {
+                    d[r][0] = d[r][1] = 0xFFFFFFFFu;
+                }
+            }
+            if ((all & 0x80008000u) != 0x80008000u) {  // some result of this thread is positive
+#pragma unroll
+                for (int r = 0; r < FM_RT; r++) {
+                    if (((d[r][0] & d[r][1]) & 0x80008000u) == 0x80008000u) continue;
+#pragma unroll
+                    for (int h = 0; h < 4; h++) {
+                        const uint32_t reg = d[r][h >> 1];
+                        if ((reg >> ((h & 1) ? 31 : 15)) & 1u) continue;
+                        const uint32_t row = (uint32_t)(r * 16 + g + (h >> 1) * 8);
+                        const uint32_t col = wrel + 2u * (uint32_t)t + (uint32_t)(h & 1);
+                        if (row < nq && col < nw)
+                            stage_push<FUSED>(A, stage, cnt, ((uint64_t)(q0 + row) << 32) | (uint64_t)(w0 + col), S.k,
+                                              S.metric);
+                    }
+                }
+            }
+            __syncwarp();
+            if (*cnt >= FT_STAGE / 2) {
+                if (FUSED) verify_stage(A, stage, cnt, lane, S.k, S.metric);
+                else flush_stage(A, stage, cnt, lane);
+            }
+        }
+        if (FUSED) verify_stage(A, stage, cnt, lane, S.k, S.metric);
+        __syncthreads();
+    }
+    if (!FUSED) flush_stage(A, stage, cnt, lane);
+}
+
+template <int W, bool FUSED>
+static int launch_mma(const FilterArgs &A, cudaStream_t st) {
+    static int grid = 0;
+    if (grid == 0) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_mma<W, FUSED>, FT_THREADS, 0);
+        grid = sm_count() * (per_sm > 0 ? per_sm : 1);
+    }
+    k_filter_mma<W, FUSED><<<grid, FT_THREADS, 0, st>>>(A);
+    FP_LAUNCHED(FUSED ? "k_filter_mma(fused)" : "k_filter_mma");
+    return FP_OK;
+}
+
 template <int W, int V, bool POS, bool FUSED>
 static int launch_one(const FilterArgs &A, bool k1mix, cudaStream_t st) {
     static int grid[2] = {0, 0};
@@ -552,6 +715,7 @@ static int launch_one(const FilterArgs &A, bool k1mix, cudaStream_t st) {
 template <bool FUSED>
 static int dispatch(const FilterArgs &A, const FpParams &fp, const FilterCfg &cfg, cudaStream_t st) {
     const bool pos = fp.type == FP_POS;
+    if (cfg.mma && !pos) return fp.width == 32 ? launch_mma<32, FUSED>(A, st) : launch_mma<16, FUSED>(A, st);
     // the mixed POPC / ALU test applies to 32-bit popcount-type fingerprints at k = 1
     const bool mix = cfg.k1mix && fp.width == 32 && !pos;
     if (FUSED) {  // the fused form is built for 4 words per thread only
@@ -570,6 +734,16 @@ static int dispatch(const FilterArgs &A, const FpParams &fp, const FilterCfg &cf
 }
 
 int tile_words(int width, int v) { return (width == 32 ? v : 2 * v) * FT_THREADS; }
+
+void tile_shape(const FilterCfg &cfg, const FpParams &fp, int *tq, int *tw) {
+    if (cfg.mma && fp.type != FP_POS) {
+        *tq = FM_TQ;
+        *tw = FM_TW;
+    } else {
+        *tq = cfg.tq < 1 ? 1 : (cfg.tq > FT_MAX_TQ ? FT_MAX_TQ : cfg.tq);
+        *tw = tile_words(fp.width, cfg.v);
+    }
+}
 
 static FilterArgs make_args(const Bucketed &q, const Bucketed &d, const QueryPlan &plan, const FpParams &fp,
                             const FilterCfg &cfg) {

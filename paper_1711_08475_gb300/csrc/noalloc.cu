@@ -173,12 +173,15 @@ extern "C" int fp_query_noalloc(fp_index *ix, const uint8_t *chars, const int64_
     FP_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int32_t), st));
     FP_CUDA(cudaMemcpyAsync(d_group, group, sizeof(group), cudaMemcpyHostToDevice, st));
     FP_TRY(bucketize_into(chars, offsets, n_queries, ends[1], nullptr, 1, ix->d_map, ix->P, st, &Q, S, d_err));
-    FilterCfg cfg;
+    FilterCfg cfg{};
     cfg.mode = FP_MODE_TILED;
     cfg.tq = 256;
     cfg.v = 4;
     cfg.k1mix = k == 1;
-    FP_TRY(plan_segments(Q, ix->D, d_group, d_group + 1, cfg.tq, tile_words(ix->P.width, cfg.v), &plan, st));
+    cfg.mma = false;
+    int tq = 0, tw = 0;
+    tile_shape(cfg, ix->P, &tq, &tw);
+    FP_TRY(plan_segments(Q, ix->D, d_group, d_group + 1, tq, tw, &plan, st));
     FP_TRY(launch_filter(Q, ix->D, plan, ix->P, cfg, surv, MAXS, st, nullptr));
     FP_TRY(launch_verify(Q, ix->D, surv, plan.scal + 4, MAXS, k, metric, ix->idx_bits, matches, plan.scal + 5,
                          MAXM, st));

@@ -144,8 +144,9 @@ int pipe_enqueue(fp_index *ix, const FilterCfg &cfg, Pipe &p, int64_t n, int64_t
     FP_TRY(bucketize_into(p.d_chars, p.d_off, n, total, p.d_group, n_groups, ix->d_map, ix->P, st, &p.Q, p.S,
                           p.d_err));
     p.qp.max_segments = nbins * 31;
-    FP_TRY(plan_segments(p.Q, ix->D, p.d_group_km, p.d_group_km + MAX_GROUPS, cfg.tq, tile_words(ix->P.width, cfg.v),
-                         &p.qp, st));
+    int tq = 0, tw = 0;
+    tile_shape(cfg, ix->P, &tq, &tw);
+    FP_TRY(plan_segments(p.Q, ix->D, p.d_group_km, p.d_group_km + MAX_GROUPS, tq, tw, &p.qp, st));
     if (ev) FP_CUDA(cudaEventRecord(ev[1], st));
     FP_TRY(launch_fused(p.Q, ix->D, p.qp, ix->P, cfg, ix->idx_bits, p.matches, p.match_cap, st, nullptr));
     if (ev) FP_CUDA(cudaEventRecord(ev[2], st));
@@ -194,6 +195,7 @@ int fp_plan_create(fp_index *ix, int64_t max_queries, int64_t max_chars, int32_t
     p->cfg.v = 4;
     p->cfg.tq = o.tile_queries > 0 ? std::min(o.tile_queries, 256) : 256;
     p->cfg.k1mix = o.variant == 0;  // the kernel takes the mixed test only in k = 1 tiles
+    p->cfg.mma = o.variant == 2;
     p->use_graph = o.mode != FP_MODE_PLAIN;  // FP_MODE_PLAIN here means: run the pipeline without a graph
     int rc = FP_OK;
     if (cudaStreamCreateWithFlags(&p->st, cudaStreamNonBlocking) != cudaSuccess ||

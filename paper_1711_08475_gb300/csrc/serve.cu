@@ -406,6 +406,7 @@ int fp_server_create(fp_index *ix, const fp_server_opts *opts, fp_server **out) 
     S->cfg.v = 4;
     S->cfg.tq = o.tile_queries > 0 ? std::min(o.tile_queries, 256) : 256;
     S->cfg.k1mix = o.variant == 0;
+    S->cfg.mma = o.variant == 2;
     cudaGetDevice(&S->device);
     if (o.memory_budget == 0) {
         size_t fr = 0, tot = 0;
