@@ -38,7 +38,7 @@ WORKLOAD = ("english1m: 1,000,000 English-like words (lognormal lengths mean 8, 
             "(60% one-edit mutations) answered under Ham and Lev, k=1, count32 fingerprint")
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=8.0, help="span of the Poisson arrivals")
     ap.add_argument("--no-url", action="store_true", help="skip the learned-map and serving legs")
     ap.add_argument("--variant", type=int, default=0, help="filter variant (fp_query_opts.variant)")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 class ClockSampler:
@@ -125,6 +125,18 @@ def dist_setup(args):
         dist.init_process_group(backend)
         pg = dist
     return world, rank, local, pg
+
+
+def rank_queries(w, rank: int, metrics=("ham", "lev")):
+    """This rank's shard of the query stream: rank 0 answers the workload's own
+    batch, rank r > 0 a batch drawn the same way from its own seeded streams
+    (same dictionary, same size and mix), so every rank does the same amount of
+    distinct work and no data crosses ranks."""
+    import datagen
+    if rank == 0:
+        return {m: w.queries[m] for m in metrics}
+    return {m: datagen.make_queries(w.dictionary, w.law, w.seed, f"q/{m}/rank{rank}", len(w.queries[m]),
+                                    0.6, m) for m in metrics}
 
 
 def barrier(pg):
@@ -371,7 +383,7 @@ def main():
     stream = torch.cuda.current_stream()
     ix = fp.fp_build(w.dictionary, fp_type=args.fp_type, width=32)
     metrics = ("ham", "lev")
-    Qs = {m: w.queries[m] for m in metrics}
+    Qs = rank_queries(w, rank, metrics)
     dev = {m: (torch.from_numpy(Q.chars).cuda(), torch.from_numpy(Q.offsets).cuda()) for m, Q in Qs.items()}
     pinned = {m: (torch.from_numpy(Q.chars).pin_memory(), torch.from_numpy(Q.offsets).pin_memory())
               for m, Q in Qs.items()}
