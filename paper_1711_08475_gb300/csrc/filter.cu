@@ -31,7 +31,7 @@ constexpr int FT_THREADS = 256;
 constexpr int FT_WARPS = FT_THREADS / 32;
 constexpr int FT_MAX_TQ = 256;
 constexpr int FT_STAGE = 256;  // staged survivors per warp
-constexpr int FT_QUEUE = 256;  // queued (lane, query) hits per warp and 32-query batch
+constexpr int FT_QUEUE = 256;  // queued (lane, tile query) hits per warp
 
 // Tuning constants (compile-time; the defaults come from sweeps on GB300).
 #ifndef FT_MIN_BLOCKS
@@ -362,16 +362,52 @@ __device__ __forceinline__ int32_t pass_sign(const uint32_t (&w)[V], uint32_t q,
     }
 }
 
+// One round of exact re-tests: lane l takes queued hit first + l (if l <
+// count), i.e. (owner lane, tile query), fetches the owner's fingerprints with
+// shuffles and stages every pair of that query and those fingerprints that
+// passes Eq. 1.
+template <int W, int V, bool POS, bool FULL, bool FUSED>
+__device__ __forceinline__ void retest_round(const FilterArgs &A, const uint32_t *s_q, const uint16_t *queue,
+                                             uint32_t first, uint32_t count, uint32_t q0, const uint32_t (&w)[V],
+                                             uint32_t invalid, uint32_t T, uint32_t wbase, uint64_t *stage,
+                                             uint32_t *cnt, int lane, int k, int metric) {
+    constexpr int G = (W == 32) ? 4 : 8;
+    constexpr int NF = (W == 32) ? V : 2 * V;
+    const bool has = (uint32_t)lane < count;
+    const uint32_t item = has ? queue[first + lane] : ((uint32_t)lane << 8);
+    const int src = (int)(item >> 8);
+    const uint32_t jq = item & 255u;
+    uint32_t ws[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) ws[v] = __shfl_sync(0xffffffffu, w[v], src);
+    const uint32_t inv = FULL ? 0u : __shfl_sync(0xffffffffu, invalid, src);
+    if (has) {
+        uint32_t F[NF];
+        all_fd<W, V, POS, NF>(ws, s_q[jq], A.M, F);
+#pragma unroll
+        for (int i = 0; i < NF; i++)
+            if (F[i] <= T && (FULL || !((inv >> i) & 1u)))
+                stage_push<FUSED>(A, stage, cnt, ((uint64_t)(q0 + jq) << 32) | (uint64_t)(wbase + lane_offset<G>(i, src)),
+                                  k, metric);
+    }
+}
+
 // One tile's pairs for the thread: queries s_q[0 .. nq) against its NF
 // fingerprints.  FULL = every fingerprint of the thread lies inside the tile.
 // Query fingerprints are read four at a time (one 128-bit shared load), the
 // four tests are independent, and each test's sign bit is shifted into the
 // hit mask (bit b of a 32-query batch <-> query jn4 - 1 - b).
+//
+// Hits are re-tested exactly, but not one batch at a time: every lane appends
+// its (lane, query) hits to the warp's queue (one shared atomic per lane with
+// hits), and the warp re-tests the queue in rounds of 32 whenever it holds a
+// full round, so nearly every round keeps all 32 lanes busy; the last partial
+// round runs when the tile ends (the fingerprints in registers belong to it).
 template <int W, int V, bool POS, bool FULL, bool K1MIX, bool FUSED>
 __device__ __forceinline__ void scan_tile(const FilterArgs &A, const uint32_t *s_q, uint32_t nq, uint32_t q0,
                                           const uint32_t (&w)[V], uint32_t invalid, uint32_t T, uint32_t wbase,
-                                          uint64_t *stage, uint32_t *cnt, uint16_t *queue, int lane, int k,
-                                          int metric) {
+                                          uint64_t *stage, uint32_t *cnt, uint16_t *queue, uint32_t *qcnt, int lane,
+                                          int k, int metric) {
     constexpr int G = (W == 32) ? 4 : 8;
     constexpr int NF = (W == 32) ? V : 2 * V;
     const uint4 *s_q4 = reinterpret_cast<const uint4 *>(s_q);
@@ -392,43 +428,26 @@ __device__ __forceinline__ void scan_tile(const FilterArgs &A, const uint32_t *s
             hits = __funnelshift_l((uint32_t)h3, hits, 1);
         }
         hits &= ~((1u << (jn4 - jn)) - 1u);  // queries past nq in the last group of four
-        // Re-test, exactly, the queries that had a (possible) passing fingerprint.
-        // Every lane posts its (lane, query) hits to the warp's queue; then the
-        // warp's lanes take one hit each and fetch the owner's fingerprints with
-        // shuffles, so the warp spends one round per 32 hits instead of one round
-        // per hit of its busiest lane.
         const uint32_t c = __popc(hits);
-        uint32_t incl = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-        if (total != 0 && total <= FT_QUEUE) {
-            uint32_t pos = incl - c;
-            for (uint32_t h = hits; h; h &= h - 1) queue[pos++] = (uint16_t)((lane << 5) | (jn4 - 1u - (__ffs(h) - 1)));
+        const uint32_t total = __reduce_add_sync(0xffffffffu, c);
+        if (total != 0 && total <= (uint32_t)(FT_QUEUE - 32)) {  // the queue holds < 32 items here
+            if (c) {
+                uint32_t pos = atomicAdd(qcnt, c);
+                for (uint32_t h = hits; h; h &= h - 1)
+                    queue[pos++] = (uint16_t)((lane << 8) | (jb + jn4 - 1u - (__ffs(h) - 1)));
+            }
             __syncwarp();
-            for (uint32_t base = 0; base < total; base += 32) {
-                const uint32_t it = base + lane;
-                const bool has = it < total;
-                const uint32_t item = has ? queue[it] : ((uint32_t)lane << 5);
-                const int src = (int)(item >> 5);
-                const uint32_t jj = item & 31u;
-                uint32_t ws[V];
-#pragma unroll
-                for (int v = 0; v < V; v++) ws[v] = __shfl_sync(0xffffffffu, w[v], src);
-                const uint32_t inv = FULL ? 0u : __shfl_sync(0xffffffffu, invalid, src);
-                if (has) {
-                    uint32_t F[NF];
-                    all_fd<W, V, POS, NF>(ws, s_q[jb + jj], A.M, F);
-#pragma unroll
-                    for (int i = 0; i < NF; i++)
-                        if (F[i] <= T && (FULL || !((inv >> i) & 1u)))
-                            stage_push<FUSED>(A, stage, cnt,
-                                              ((uint64_t)(q0 + jb + jj) << 32) | (uint64_t)(wbase + lane_offset<G>(i, src)),
-                                              k, metric);
-                }
+            const uint32_t qn = *qcnt;
+            uint32_t done = 0;
+            for (; qn - done >= 32u; done += 32u)
+                retest_round<W, V, POS, FULL, FUSED>(A, s_q, queue, done, 32u, q0, w, invalid, T, wbase, stage, cnt,
+                                                     lane, k, metric);
+            if (done) {  // move the rest (< 32) to the front
+                const uint32_t rem = qn - done;
+                const uint16_t keep = (uint32_t)lane < rem ? queue[done + lane] : (uint16_t)0;
+                __syncwarp();
+                if ((uint32_t)lane < rem) queue[lane] = keep;
+                if (lane == 0) *qcnt = rem;
             }
             __syncwarp();
         } else if (total != 0) {  // very many hits (large k, dense matches): each lane re-tests its own
@@ -452,6 +471,15 @@ __device__ __forceinline__ void scan_tile(const FilterArgs &A, const uint32_t *s
             else flush_stage(A, stage, cnt, lane);
         }
     }
+    // the last partial round of this tile
+    const uint32_t qn = *qcnt;
+    if (qn) {
+        retest_round<W, V, POS, FULL, FUSED>(A, s_q, queue, 0u, qn, q0, w, invalid, T, wbase, stage, cnt, lane, k,
+                                             metric);
+        __syncwarp();
+        if (lane == 0) *qcnt = 0;
+        __syncwarp();
+    }
 }
 
 // W: fingerprint width; V: 32-bit words per thread (multiple of 4).
@@ -464,6 +492,7 @@ __global__ void __launch_bounds__(FT_THREADS, FT_MIN_BLOCKS) k_filter_tiled(Filt
     __shared__ uint64_t s_stage[FT_WARPS][FT_STAGE];
     __shared__ uint32_t s_cnt[FT_WARPS];
     __shared__ uint16_t s_queue[FT_WARPS][FT_QUEUE];
+    __shared__ uint32_t s_qcnt[FT_WARPS];
     __shared__ uint64_t s_tile;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nseg = (int)A.scal[0];
@@ -471,7 +500,11 @@ __global__ void __launch_bounds__(FT_THREADS, FT_MIN_BLOCKS) k_filter_tiled(Filt
     uint64_t *stage = s_stage[warp];
     uint32_t *cnt = &s_cnt[warp];
     uint16_t *queue = s_queue[warp];
-    if (lane == 0) *cnt = 0;
+    uint32_t *qcnt = &s_qcnt[warp];
+    if (lane == 0) {
+        *cnt = 0;
+        *qcnt = 0;
+    }
     __syncwarp();
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd((unsigned long long *)&A.scal[3], 1ull);
@@ -512,16 +545,16 @@ __global__ void __launch_bounds__(FT_THREADS, FT_MIN_BLOCKS) k_filter_tiled(Filt
             if (lane_offset<G>(i, lane) >= nvalid) invalid |= 1u << i;
         if (K1MIX && T != 2u) {  // a k = 1 variant given another k: exact general path
             if (nw == (uint32_t)TW)
-                scan_tile<W, V, POS, true, false, FUSED>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, queue, lane,
+                scan_tile<W, V, POS, true, false, FUSED>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, queue, qcnt, lane,
                                                            S.k, S.metric);
             else
-                scan_tile<W, V, POS, false, false, FUSED>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, queue, lane,
+                scan_tile<W, V, POS, false, false, FUSED>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, queue, qcnt, lane,
                                                            S.k, S.metric);
         } else if (nw == (uint32_t)TW) {
-            scan_tile<W, V, POS, true, K1MIX, FUSED>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, queue, lane,
+            scan_tile<W, V, POS, true, K1MIX, FUSED>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, queue, qcnt, lane,
                                                            S.k, S.metric);
         } else {
-            scan_tile<W, V, POS, false, K1MIX, FUSED>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, queue, lane,
+            scan_tile<W, V, POS, false, K1MIX, FUSED>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, queue, qcnt, lane,
                                                            S.k, S.metric);
         }
         // fused: the next tile may have another (k, metric), so verify what is staged

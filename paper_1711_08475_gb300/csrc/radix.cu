@@ -42,40 +42,67 @@ __global__ void __launch_bounds__(RB_THREADS) k_radix_hist(const uint64_t *__res
     hist[(size_t)threadIdx.x * nb + b] = h[threadIdx.x];
 }
 
-// Exclusive scan of n uint32 values in place, one block of 1024 threads that
-// walks the array in coalesced rounds of 1024 (warp shuffles inside a warp,
-// one shared step across the 32 warps, a carry between rounds).
+// Exclusive scan of n uint32 values in place with one block of 1024 threads,
+// in tiles of 8192 values: a tile is loaded with coalesced reads (eight loads
+// per thread in flight at once) into shared memory, thread t scans the eight
+// consecutive values [8t, 8t + 8) of the tile, the per-thread sums are scanned
+// across the block (warp shuffles, then one shared step over the 32 warps),
+// and the tile is written back coalesced.  Shared indices are padded by one
+// word per 32 so that both access patterns are free of bank conflicts.
+constexpr int SCAN_R = 8, SCAN_TILE = 1024 * SCAN_R;
+
+__device__ __forceinline__ int scan_pad(int j) { return j + (j >> 5); }
+
 __global__ void __launch_bounds__(1024) k_scan_u32(uint32_t *__restrict__ a, int64_t n) {
+    __shared__ uint32_t s[SCAN_TILE + SCAN_TILE / 32];
     __shared__ uint32_t s_warp[32];
     __shared__ uint32_t s_carry;
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     if (t == 0) s_carry = 0;
-    __syncthreads();
-    for (int64_t base = 0; base < n; base += 1024) {
-        const int64_t i = base + t;
-        const uint32_t v = i < n ? a[i] : 0u;
-        uint32_t x = v;  // inclusive scan within the warp
+    for (int64_t base = 0; base < n; base += SCAN_TILE) {
+#pragma unroll
+        for (int r = 0; r < SCAN_R; r++) {
+            const int64_t i = base + r * 1024 + t;
+            s[scan_pad(r * 1024 + t)] = i < n ? a[i] : 0u;
+        }
+        __syncthreads();
+        uint32_t v[SCAN_R], sum = 0;
+#pragma unroll
+        for (int r = 0; r < SCAN_R; r++) {
+            v[r] = s[scan_pad(t * SCAN_R + r)];
+            sum += v[r];
+        }
+        uint32_t x = sum;  // inclusive scan of the thread sums within the warp
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
         if (lane == 31) s_warp[w] = x;
         __syncthreads();
         if (w == 0) {
-            uint32_t s = s_warp[lane];
+            uint32_t q = s_warp[lane];
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
-                if (lane >= o) s += y;
+                const uint32_t y = __shfl_up_sync(0xffffffffu, q, o);
+                if (lane >= o) q += y;
             }
-            s_warp[lane] = s;  // inclusive over warps
+            s_warp[lane] = q;  // inclusive over warps
         }
         __syncthreads();
         const uint32_t carry = s_carry;
-        const uint32_t before = (w ? s_warp[w - 1] : 0u) + x - v;
-        if (i < n) a[i] = carry + before;
+        uint32_t run = carry + (w ? s_warp[w - 1] : 0u) + x - sum;
+#pragma unroll
+        for (int r = 0; r < SCAN_R; r++) {
+            s[scan_pad(t * SCAN_R + r)] = run;
+            run += v[r];
+        }
         __syncthreads();
+#pragma unroll
+        for (int r = 0; r < SCAN_R; r++) {
+            const int64_t i = base + r * 1024 + t;
+            if (i < n) a[i] = s[scan_pad(r * 1024 + t)];
+        }
         if (t == 1023) s_carry = carry + s_warp[31];
         __syncthreads();
     }
