@@ -34,14 +34,24 @@ constexpr int FT_STAGE = 256;  // staged survivors per warp
 constexpr int FT_QUEUE = 256;  // queued (lane, tile query) hits per warp
 
 // Tuning constants (compile-time; the defaults come from sweeps on GB300).
+// Resident blocks per SM the register budget is set for: the 32-bit,
+// 4-words-per-thread filter fits 32 registers without spilling (8 blocks, 64
+// warps); the other shapes keep 48; the fused form, which calls the verifier,
+// is fastest at 64 registers (4 blocks; a few spills, measured against 3 and 5).
 #ifndef FT_MIN_BLOCKS
-#define FT_MIN_BLOCKS 5  // resident blocks per SM the register budget is set for
+#define FT_MIN_BLOCKS 5
+#endif
+#ifndef FT_MAIN_MIN_BLOCKS
+#define FT_MAIN_MIN_BLOCKS 8
+#endif
+#ifndef FT_FUSED_MIN_BLOCKS
+#define FT_FUSED_MIN_BLOCKS 4
 #endif
 #ifndef FT_MIX_DIV
 #define FT_MIX_DIV 4  // k = 1 mix: V / FT_MIX_DIV of a thread's words use the ALU-only test
 #endif
 #ifndef FT_UNROLL
-#define FT_UNROLL 2  // groups of four queries unrolled in the hot loop
+#define FT_UNROLL 1  // groups of four queries unrolled in the hot loop
 #endif
 #define FT_STR(x) #x
 #define FT_UNROLL_PRAGMA(n) _Pragma(FT_STR(unroll n))
@@ -482,9 +492,14 @@ __device__ __forceinline__ void scan_tile(const FilterArgs &A, const uint32_t *s
     }
 }
 
+template <int W, int V, bool POS, bool FUSED>
+constexpr int ft_min_blocks() {
+    return FUSED ? FT_FUSED_MIN_BLOCKS : ((W == 32 && V == 4 && !POS) ? FT_MAIN_MIN_BLOCKS : FT_MIN_BLOCKS);
+}
+
 // W: fingerprint width; V: 32-bit words per thread (multiple of 4).
 template <int W, int V, bool POS, bool K1MIX, bool FUSED>
-__global__ void __launch_bounds__(FT_THREADS, FT_MIN_BLOCKS) k_filter_tiled(FilterArgs A) {
+__global__ void __launch_bounds__(FT_THREADS, (ft_min_blocks<W, V, POS, FUSED>())) k_filter_tiled(FilterArgs A) {
     constexpr int G = (W == 32) ? 4 : 8;             // fingerprints per 128-bit vector
     constexpr int NF = (W == 32) ? V : 2 * V;        // fingerprints per thread
     constexpr int TW = NF * FT_THREADS;              // fingerprints per tile
