@@ -51,7 +51,7 @@ constexpr int FT_QUEUE = 256;  // queued (lane, tile query) hits per warp
 #define FT_MIX_DIV 4  // k = 1 mix: V / FT_MIX_DIV of a thread's words use the ALU-only test
 #endif
 #ifndef FT_UNROLL
-#define FT_UNROLL 1  // groups of four queries unrolled in the hot loop
+#define FT_UNROLL 1  // groups of four queries unrolled in the loop over a partial batch
 #endif
 #define FT_STR(x) #x
 #define FT_UNROLL_PRAGMA(n) _Pragma(FT_STR(unroll n))
@@ -372,6 +372,21 @@ __device__ __forceinline__ int32_t pass_sign(const uint32_t (&w)[V], uint32_t q,
     }
 }
 
+// Four queries (one 128-bit shared load) against the thread's fingerprints;
+// each test's sign bit is shifted into the hit mask.
+template <int W, int V, bool POS, bool FULL, bool K1MIX>
+__device__ __forceinline__ uint32_t four_queries(const uint32_t (&w)[V], uint4 q4, const PosMasks &M, uint32_t invalid,
+                                                 uint32_t T, uint32_t hits) {
+    const int32_t h0 = pass_sign<W, V, POS, FULL, K1MIX>(w, q4.x, M, invalid, T);
+    const int32_t h1 = pass_sign<W, V, POS, FULL, K1MIX>(w, q4.y, M, invalid, T);
+    const int32_t h2 = pass_sign<W, V, POS, FULL, K1MIX>(w, q4.z, M, invalid, T);
+    const int32_t h3 = pass_sign<W, V, POS, FULL, K1MIX>(w, q4.w, M, invalid, T);
+    hits = __funnelshift_l((uint32_t)h0, hits, 1);
+    hits = __funnelshift_l((uint32_t)h1, hits, 1);
+    hits = __funnelshift_l((uint32_t)h2, hits, 1);
+    return __funnelshift_l((uint32_t)h3, hits, 1);
+}
+
 // One round of exact re-tests: lane l takes queued hit first + l (if l <
 // count), i.e. (owner lane, tile query), fetches the owner's fingerprints with
 // shuffles and stages every pair of that query and those fingerprints that
@@ -425,17 +440,14 @@ __device__ __forceinline__ void scan_tile(const FilterArgs &A, const uint32_t *s
         const uint32_t jn = min(32u, nq - jb);
         const uint32_t jn4 = (jn + 3u) & ~3u;
         uint32_t hits = 0;
-        FT_UNROLL_PRAGMA(FT_UNROLL)
-        for (uint32_t jj = 0; jj < jn; jj += 4) {
-            const uint4 q4 = s_q4[(jb + jj) >> 2];
-            const int32_t h0 = pass_sign<W, V, POS, FULL, K1MIX>(w, q4.x, A.M, invalid, T);
-            const int32_t h1 = pass_sign<W, V, POS, FULL, K1MIX>(w, q4.y, A.M, invalid, T);
-            const int32_t h2 = pass_sign<W, V, POS, FULL, K1MIX>(w, q4.z, A.M, invalid, T);
-            const int32_t h3 = pass_sign<W, V, POS, FULL, K1MIX>(w, q4.w, A.M, invalid, T);
-            hits = __funnelshift_l((uint32_t)h0, hits, 1);
-            hits = __funnelshift_l((uint32_t)h1, hits, 1);
-            hits = __funnelshift_l((uint32_t)h2, hits, 1);
-            hits = __funnelshift_l((uint32_t)h3, hits, 1);
+        if (jn == 32u) {  // a whole batch: fully unrolled
+#pragma unroll
+            for (uint32_t jj = 0; jj < 32u; jj += 4)
+                hits = four_queries<W, V, POS, FULL, K1MIX>(w, s_q4[(jb + jj) >> 2], A.M, invalid, T, hits);
+        } else {
+            FT_UNROLL_PRAGMA(FT_UNROLL)
+            for (uint32_t jj = 0; jj < jn; jj += 4)
+                hits = four_queries<W, V, POS, FULL, K1MIX>(w, s_q4[(jb + jj) >> 2], A.M, invalid, T, hits);
         }
         hits &= ~((1u << (jn4 - jn)) - 1u);  // queries past nq in the last group of four
         const uint32_t c = __popc(hits);

@@ -45,36 +45,82 @@ struct VerifyArgs {
     uint64_t match_cap;
 };
 
+// Survivors per thread: a thread gathers the records, lengths and row offsets
+// of VU survivors (and, for Hamming, the first 16 bytes of both rows) before
+// it verifies any of them, so that VU independent chains of dependent loads
+// are in flight instead of one.
+#ifndef VERIFY_U
+#define VERIFY_U 4
+#endif
+
 // metric 0: Hamming with runtime k; metric 1: Levenshtein with K.
 template <int METRIC, int K>
 __global__ void __launch_bounds__(256) k_verify(VerifyArgs A, int k) {
+    constexpr int U = VERIFY_U;
     const int lane = threadIdx.x & 31;
     const uint64_t n0 = *A.n_surv;
     const uint64_t n = n0 < A.surv_cap ? n0 : A.surv_cap;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x * U;
     const unsigned lt = (1u << lane) - 1u;
-    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n; base += stride) {
-        const uint64_t i = base + lane;
-        bool hit = false;
-        uint64_t key = 0;
-        if (i < n) {
-            const uint64_t s = A.surv[i];
-            const uint32_t qs = (uint32_t)(s >> 32), ds = (uint32_t)s;
-            const int m = A.q_len[qs], L = A.d_len[ds];
-            const uint8_t *qa = A.q_str + (uint64_t)A.q_row16[qs] * 16;
-            const uint8_t *da = A.d_str + (uint64_t)A.d_row16[ds] * 16;
-            if (METRIC == FP_HAM) hit = (m == L) && ham_within(qa, da, m, k);
-            else hit = (m - L <= K && L - m <= K) && lev_within<K>(qa, m, da, L);
-            if (hit) key = ((uint64_t)(uint32_t)A.q_idx[qs] << A.idx_bits) | (uint64_t)(uint32_t)A.d_idx[ds];
+    for (uint64_t base = ((uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u)) * U; base < n; base += stride) {
+        // survivor base + 32 u + lane for u < U: each of the U loads is coalesced
+        uint64_t s[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const uint64_t i = base + 32u * u + lane;
+            s[u] = i < n ? A.surv[i] : ~0ull;
         }
-        const unsigned bal = __ballot_sync(0xffffffffu, hit);
-        if (bal) {
-            unsigned long long mb = 0;
-            if (lane == 0) mb = atomicAdd((unsigned long long *)A.n_matches, (unsigned long long)__popc(bal));
-            mb = __shfl_sync(0xffffffffu, mb, 0);
-            if (hit) {
-                const uint64_t pos = mb + __popc(bal & lt);
-                if (pos < A.match_cap) A.matches[pos] = key;
+        int m[U], L[U];
+        uint32_t qr[U], dr[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            if (s[u] != ~0ull) {
+                const uint32_t qs = (uint32_t)(s[u] >> 32), ds = (uint32_t)s[u];
+                m[u] = A.q_len[qs];
+                L[u] = A.d_len[ds];
+                qr[u] = A.q_row16[qs];
+                dr[u] = A.d_row16[ds];
+            } else {
+                m[u] = -1;
+                L[u] = -2;
+                qr[u] = dr[u] = 0;
+            }
+        }
+        bool hit[U];
+        if (METRIC == FP_HAM) {
+            uint4 x[U], y[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                if (m[u] == L[u] && m[u] > 0) {
+                    x[u] = *(const uint4 *)(A.q_str + (uint64_t)qr[u] * 16);
+                    y[u] = *(const uint4 *)(A.d_str + (uint64_t)dr[u] * 16);
+                } else {
+                    x[u] = y[u] = make_uint4(0u, 0u, 0u, 0u);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++)
+                hit[u] = m[u] == L[u] && ham_within_first(x[u], y[u], A.q_str + (uint64_t)qr[u] * 16,
+                                                          A.d_str + (uint64_t)dr[u] * 16, m[u], k);
+        } else {
+#pragma unroll
+            for (int u = 0; u < U; u++)
+                hit[u] = m[u] >= 0 && m[u] - L[u] <= K && L[u] - m[u] <= K &&
+                         lev_within<K>(A.q_str + (uint64_t)qr[u] * 16, m[u], A.d_str + (uint64_t)dr[u] * 16, L[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const unsigned bal = __ballot_sync(0xffffffffu, hit[u]);
+            if (bal) {
+                unsigned long long mb = 0;
+                if (lane == 0) mb = atomicAdd((unsigned long long *)A.n_matches, (unsigned long long)__popc(bal));
+                mb = __shfl_sync(0xffffffffu, mb, 0);
+                if (hit[u]) {
+                    const uint32_t qs = (uint32_t)(s[u] >> 32), ds = (uint32_t)s[u];
+                    const uint64_t key = ((uint64_t)(uint32_t)A.q_idx[qs] << A.idx_bits) | (uint64_t)(uint32_t)A.d_idx[ds];
+                    const uint64_t pos = mb + __popc(bal & lt);
+                    if (pos < A.match_cap) A.matches[pos] = key;
+                }
             }
         }
     }

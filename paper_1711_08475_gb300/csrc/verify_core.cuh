@@ -24,6 +24,21 @@ __device__ __forceinline__ bool ham_within(const uint8_t *a, const uint8_t *b, i
     return true;
 }
 
+// ham_within with the first 16 bytes of both rows already loaded (x, y).
+__device__ __forceinline__ bool ham_within_first(uint4 x, uint4 y, const uint8_t *a, const uint8_t *b, int len, int k) {
+    int mism = __popc(~zero_byte_mask(x.x ^ y.x) & 0x80808080u) + __popc(~zero_byte_mask(x.y ^ y.y) & 0x80808080u) +
+               __popc(~zero_byte_mask(x.z ^ y.z) & 0x80808080u) + __popc(~zero_byte_mask(x.w ^ y.w) & 0x80808080u);
+    if (mism > k) return false;
+    const uint4 *A = (const uint4 *)a, *B = (const uint4 *)b;
+    for (int c = 16; c < len; c += 16) {
+        const uint4 p = A[c >> 4], q = B[c >> 4];
+        mism += __popc(~zero_byte_mask(p.x ^ q.x) & 0x80808080u) + __popc(~zero_byte_mask(p.y ^ q.y) & 0x80808080u) +
+                __popc(~zero_byte_mask(p.z ^ q.z) & 0x80808080u) + __popc(~zero_byte_mask(p.w ^ q.w) & 0x80808080u);
+        if (mism > k) return false;
+    }
+    return true;
+}
+
 template <int K>
 __device__ __forceinline__ bool lev_within(const uint8_t *a, int m, const uint8_t *b, int n) {
     constexpr int BAND = 2 * K + 1;
