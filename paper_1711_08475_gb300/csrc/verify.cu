@@ -54,14 +54,40 @@ struct VerifyArgs {
 #endif
 
 // metric 0: Hamming with runtime k; metric 1: Levenshtein with K.
+// Matches are staged per warp in shared memory and appended to the global
+// list with one atomic reservation per VSTAGE / 2 or more, not one per round.
+constexpr int VSTAGE = 256;
+
+__device__ __forceinline__ void flush_matches(const VerifyArgs &A, uint64_t *stage, uint32_t *cnt, int lane) {
+    __syncwarp();
+    const uint32_t c = min(*cnt, (uint32_t)VSTAGE);
+    unsigned long long base = 0;
+    if (lane == 0 && c) base = atomicAdd((unsigned long long *)A.n_matches, (unsigned long long)c);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (uint32_t i = lane; i < c; i += 32) {
+        const uint64_t pos = base + i;
+        if (pos < A.match_cap) A.matches[pos] = stage[i];
+    }
+    __syncwarp();
+    if (lane == 0) *cnt = 0;
+    __syncwarp();
+}
+
 template <int METRIC, int K>
 __global__ void __launch_bounds__(256) k_verify(VerifyArgs A, int k) {
     constexpr int U = VERIFY_U;
-    const int lane = threadIdx.x & 31;
+    __shared__ uint64_t s_stage[8][VSTAGE];
+    __shared__ uint32_t s_cnt[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t *stage = s_stage[warp];
+    uint32_t *cnt = &s_cnt[warp];
+    if (lane == 0) *cnt = 0;
+    __syncwarp();
     const uint64_t n0 = *A.n_surv;
     const uint64_t n = n0 < A.surv_cap ? n0 : A.surv_cap;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x * U;
     const unsigned lt = (1u << lane) - 1u;
+    static_assert(VSTAGE / 2 + 32 * VERIFY_U <= VSTAGE, "a round of matches must fit the stage");
     for (uint64_t base = ((uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u)) * U; base < n; base += stride) {
         // survivor base + 32 u + lane for u < U: each of the U loads is coalesced
         uint64_t s[U];
@@ -112,18 +138,20 @@ __global__ void __launch_bounds__(256) k_verify(VerifyArgs A, int k) {
         for (int u = 0; u < U; u++) {
             const unsigned bal = __ballot_sync(0xffffffffu, hit[u]);
             if (bal) {
-                unsigned long long mb = 0;
-                if (lane == 0) mb = atomicAdd((unsigned long long *)A.n_matches, (unsigned long long)__popc(bal));
-                mb = __shfl_sync(0xffffffffu, mb, 0);
+                const uint32_t at = *cnt;  // < VSTAGE / 2 + 32 * U <= VSTAGE
                 if (hit[u]) {
                     const uint32_t qs = (uint32_t)(s[u] >> 32), ds = (uint32_t)s[u];
-                    const uint64_t key = ((uint64_t)(uint32_t)A.q_idx[qs] << A.idx_bits) | (uint64_t)(uint32_t)A.d_idx[ds];
-                    const uint64_t pos = mb + __popc(bal & lt);
-                    if (pos < A.match_cap) A.matches[pos] = key;
+                    stage[at + __popc(bal & lt)] =
+                        ((uint64_t)(uint32_t)A.q_idx[qs] << A.idx_bits) | (uint64_t)(uint32_t)A.d_idx[ds];
                 }
+                __syncwarp();
+                if (lane == 0) *cnt = at + __popc(bal);
+                __syncwarp();
             }
         }
+        if (*cnt >= VSTAGE / 2) flush_matches(A, stage, cnt, lane);
     }
+    flush_matches(A, stage, cnt, lane);
 }
 
 template <int METRIC, int K>
