@@ -208,28 +208,32 @@ static __device__ __noinline__ bool verify_one(const FilterArgs &A, uint64_t e, 
     return hit;
 }
 
-// Fused form: verifies the warp's staged survivors, one per lane, and
-// appends the matches with one reservation per round of 32.
+// Fused form: verifies the warp's staged survivors, one per lane.  Matches
+// are compacted into the front of the same buffer (a round's survivors are in
+// registers before any of its matches is written, and a round never writes
+// past its own slots) and appended to the match list with one reservation.
 __device__ __forceinline__ void verify_stage(const FilterArgs &A, uint64_t *stage, uint32_t *cnt, int lane, int k,
                                              int metric) {
     __syncwarp();
     const uint32_t c = min(*cnt, (uint32_t)FT_STAGE);
     const unsigned lt = (1u << lane) - 1u;
     if (lane == 0 && c) atomicAdd((unsigned long long *)&A.scal[4], (unsigned long long)c);
+    uint32_t nm = 0;
     for (uint32_t base = 0; base < c; base += 32) {
         const uint32_t i = base + lane;
         uint64_t key = 0;
         const bool hit = i < c && verify_one(A, stage[i], k, metric, &key);
         const unsigned bal = __ballot_sync(0xffffffffu, hit);
-        if (bal) {
-            unsigned long long mb = 0;
-            if (lane == 0) mb = atomicAdd((unsigned long long *)&A.scal[5], (unsigned long long)__popc(bal));
-            mb = __shfl_sync(0xffffffffu, mb, 0);
-            if (hit) {
-                const uint64_t pos = mb + __popc(bal & lt);
-                if (pos < A.match_cap) A.matches[pos] = key;
-            }
-        }
+        if (hit) stage[nm + __popc(bal & lt)] = key;
+        nm += __popc(bal);
+        __syncwarp();
+    }
+    if (nm) {
+        unsigned long long mb = 0;
+        if (lane == 0) mb = atomicAdd((unsigned long long *)&A.scal[5], (unsigned long long)nm);
+        mb = __shfl_sync(0xffffffffu, mb, 0);
+        for (uint32_t j = lane; j < nm; j += 32)
+            if (mb + j < A.match_cap) A.matches[mb + j] = stage[j];
     }
     __syncwarp();
     if (lane == 0) *cnt = 0;
@@ -440,7 +444,7 @@ __device__ __forceinline__ void scan_tile(const FilterArgs &A, const uint32_t *s
         const uint32_t jn = min(32u, nq - jb);
         const uint32_t jn4 = (jn + 3u) & ~3u;
         uint32_t hits = 0;
-        if (jn == 32u) {  // a whole batch: fully unrolled
+        if (!FUSED && jn == 32u) {  // a whole batch: fully unrolled (the fused form is faster without)
 #pragma unroll
             for (uint32_t jj = 0; jj < 32u; jj += 4)
                 hits = four_queries<W, V, POS, FULL, K1MIX>(w, s_q4[(jb + jj) >> 2], A.M, invalid, T, hits);
