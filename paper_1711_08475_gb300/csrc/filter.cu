@@ -391,6 +391,19 @@ __device__ __forceinline__ uint32_t four_queries(const uint32_t (&w)[V], uint4 q
     return __funnelshift_l((uint32_t)h3, hits, 1);
 }
 
+// Empties the warp's stage when it might not hold the passing pairs of one
+// more round (32 lanes x NF fingerprints), so that pushes never take the
+// slow per-survivor path of a full stage.  Warp-uniform.
+template <int NF, bool FUSED>
+__device__ __forceinline__ void make_room(const FilterArgs &A, uint64_t *stage, uint32_t *cnt, int lane, int k,
+                                          int metric) {
+    __syncwarp();
+    if (*cnt > (uint32_t)(FT_STAGE - 32 * NF)) {
+        if (FUSED) verify_stage(A, stage, cnt, lane, k, metric);
+        else flush_stage(A, stage, cnt, lane);
+    }
+}
+
 // One round of exact re-tests: lane l takes queued hit first + l (if l <
 // count), i.e. (owner lane, tile query), fetches the owner's fingerprints with
 // shuffles and stages every pair of that query and those fingerprints that
@@ -465,9 +478,11 @@ __device__ __forceinline__ void scan_tile(const FilterArgs &A, const uint32_t *s
             __syncwarp();
             const uint32_t qn = *qcnt;
             uint32_t done = 0;
-            for (; qn - done >= 32u; done += 32u)
+            for (; qn - done >= 32u; done += 32u) {
+                make_room<NF, FUSED>(A, stage, cnt, lane, k, metric);
                 retest_round<W, V, POS, FULL, FUSED>(A, s_q, queue, done, 32u, q0, w, invalid, T, wbase, stage, cnt,
                                                      lane, k, metric);
+            }
             if (done) {  // move the rest (< 32) to the front
                 const uint32_t rem = qn - done;
                 const uint16_t keep = (uint32_t)lane < rem ? queue[done + lane] : (uint16_t)0;
@@ -476,19 +491,24 @@ __device__ __forceinline__ void scan_tile(const FilterArgs &A, const uint32_t *s
                 if (lane == 0) *qcnt = rem;
             }
             __syncwarp();
-        } else if (total != 0) {  // very many hits (large k, dense matches): each lane re-tests its own
-            while (hits) {
-                const uint32_t b = __ffs(hits) - 1;
-                hits &= hits - 1;
-                const uint32_t jj = jn4 - 1u - b;
-                uint32_t F[NF];
-                all_fd<W, V, POS, NF>(w, s_q[jb + jj], A.M, F);
+        } else if (total != 0) {
+            // very many hits (large k, short words, dense matches): the batch's
+            // queries one at a time, each lane re-testing its own fingerprints,
+            // with room in the stage for a whole query's passes
+            for (uint32_t jj = 0; jj < jn; jj++) {
+                const bool mine = (hits >> (jn4 - 1u - jj)) & 1u;
+                if (__ballot_sync(0xffffffffu, mine) == 0u) continue;
+                make_room<NF, FUSED>(A, stage, cnt, lane, k, metric);
+                if (mine) {
+                    uint32_t F[NF];
+                    all_fd<W, V, POS, NF>(w, s_q[jb + jj], A.M, F);
 #pragma unroll
-                for (int i = 0; i < NF; i++)
-                    if (F[i] <= T && (FULL || !((invalid >> i) & 1u)))
-                        stage_push<FUSED>(A, stage, cnt,
-                                          ((uint64_t)(q0 + jb + jj) << 32) | (uint64_t)(wbase + lane_offset<G>(i, lane)),
-                                          k, metric);
+                    for (int i = 0; i < NF; i++)
+                        if (F[i] <= T && (FULL || !((invalid >> i) & 1u)))
+                            stage_push<FUSED>(
+                                A, stage, cnt,
+                                ((uint64_t)(q0 + jb + jj) << 32) | (uint64_t)(wbase + lane_offset<G>(i, lane)), k, metric);
+                }
             }
             __syncwarp();
         }
@@ -500,6 +520,7 @@ __device__ __forceinline__ void scan_tile(const FilterArgs &A, const uint32_t *s
     // the last partial round of this tile
     const uint32_t qn = *qcnt;
     if (qn) {
+        make_room<NF, FUSED>(A, stage, cnt, lane, k, metric);
         retest_round<W, V, POS, FULL, FUSED>(A, s_q, queue, 0u, qn, q0, w, invalid, T, wbase, stage, cnt, lane, k,
                                              metric);
         __syncwarp();

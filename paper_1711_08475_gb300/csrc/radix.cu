@@ -179,7 +179,8 @@ int radix_sort_u64(uint64_t *keys, uint64_t *tmp, const uint64_t *d_n, int64_t m
     *result = keys;
     if (max_n <= 0 || bits_hi <= bits_lo) return FP_OK;
     int64_t nb64 = (max_n + 4095) / 4096;
-    int nb = (int)(nb64 < 1 ? 1 : (nb64 > 256 ? 256 : nb64));
+    const int64_t cap = max_n >= (1LL << 26) ? 4096 : 256;  // more blocks only for very large sorts
+    int nb = (int)(nb64 < 1 ? 1 : (nb64 > cap ? cap : nb64));
     uint32_t *hist = nullptr;
     FP_CUDA(cudaMallocAsync((void **)&hist, sizeof(uint32_t) * 256 * (size_t)nb, st));
     uint64_t *src = keys, *dst = tmp;
@@ -227,7 +228,8 @@ namespace fpk {
 // holds 256 entries per block).
 int radix_blocks(int64_t max_n) {
     int64_t nb64 = (max_n + 4095) / 4096;
-    return (int)(nb64 < 1 ? 1 : (nb64 > 256 ? 256 : nb64));
+    const int64_t cap = max_n >= (1LL << 26) ? 4096 : 256;  // more blocks only for very large sorts
+    return (int)(nb64 < 1 ? 1 : (nb64 > cap ? cap : nb64));
 }
 
 // radix_sort_u64 with the digit histogram supplied by the caller
