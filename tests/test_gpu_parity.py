@@ -409,3 +409,67 @@ def test_autotuner(fp, english_small, tmp_path, monkeypatch):
     res = fp.fp_query_ex(ix, w.queries["lev"], k=1, metric="lev", tile_queries=o1["tile_queries"],
                          words_per_thread=o1["words_per_thread"], variant=o1["variant"])
     assert_same(res, rp0, idx0, "tuned shape")
+
+
+# ---------------------------------------------------------------------------
+# the batched and the serving workloads at full size, sampled
+# ---------------------------------------------------------------------------
+
+
+def test_batched10m_full_sampled(fp):
+    """10,000,000 words, 256 uneven batches (k in {1, 2}, Ham and Lev) in one
+    captured plan with the autotuned tile, as the benchmark runs it; sampled
+    patterns of every (k, metric) pair against the oracle."""
+    from paper_1711_08475_gb300 import tune
+    w, batches = datagen.batched10m()
+    ix = fp.fp_build(w.dictionary, fp_type="count", width=32)
+    allq = datagen.Strings.concat([b.queries for b in batches])
+    spec = [(len(b.queries), b.k, b.metric) for b in batches]
+    sample = datagen.Strings.concat([b.queries for b in batches if (b.k, b.metric) == (1, "lev")])
+    opts = tune.tuned_opts(ix, sample.subset(np.arange(min(len(sample), 20000))), k=1, metric="lev", mode="fused",
+                           reps=1)
+    plan = fp.Plan(ix, len(allq), len(allq.chars), len(spec), tile_queries=opts["tile_queries"],
+                   variant=opts["variant"])
+    r = plan.run(allq, batches=spec)
+    rp, idx = r.csr()
+    st = r.stats()
+    plan.free()
+    assert rp[0] == 0 and np.all(np.diff(rp) >= 0) and rp[-1] == len(idx) == st["matches"]
+    base, picks = 0, {}
+    for n, k, metric in spec:
+        sel = picks.setdefault((k, metric), [])
+        if n and len(sel) < 12:
+            sel.extend(sorted({base, base + n // 2, base + n - 1}))
+        base += n
+    for (k, metric), rows in picks.items():
+        rows = np.array(sorted(set(rows)), np.int64)
+        rp0, idx0 = oracle.match(w.dictionary, allq.subset(rows), k, metric)
+        for j, q in enumerate(rows):
+            assert np.array_equal(idx[rp[q]:rp[q + 1]], idx0[rp0[j]:rp0[j + 1]]), (k, metric, q)
+
+
+def test_serving5m_full_sampled(fp):
+    """5,000,000 URL-like strings with a learned map, the Poisson request stream
+    replayed against the server (arrival times compressed to 1 s); sampled
+    patterns against the oracle, and the same rows as the frequency index."""
+    w, reqs = datagen.serving5m()
+    freq = fp.fp_build(w.dictionary, fp_type="occ", width=32)
+    train = datagen.make_queries(w.dictionary, w.law, w.seed, "train/lev", 20000, 0.5, "lev")
+    s = fp.fp_sample_pairs(freq, train, k=1, metric="lev", n_samples=400000, seed=11)
+    mp, _, _ = fp.fp_learn_map(32, s["masks"], s["match"], k=1, seed=3)
+    lrn = fp.fp_build(w.dictionary, fp_type="occ", width=32, custom_map=mp)
+    allq = datagen.Strings.concat([r.queries for r in reqs])
+    sizes = [len(r.queries) for r in reqs]
+    last = max(r.arrival_s for r in reqs) or 1.0
+    arrive = np.array([int(r.arrival_s / last * 1e6) for r in reqs], np.int64)
+    srv = fp.Server(lrn, lanes=4)
+    res, lat = srv.replay(allq, request_sizes=sizes, arrival_us=arrive, k=1, metric="lev")
+    srv.free()
+    rp, idx = res.csr()
+    rpf, idxf = fp.fp_query(freq, allq, k=1, metric="lev").csr()
+    assert np.array_equal(rp, rpf) and np.array_equal(idx, idxf)
+    pick = np.arange(0, len(allq), max(1, len(allq) // 40))
+    rp0, idx0 = oracle.match(w.dictionary, allq.subset(pick), 1, "lev")
+    for j, q in enumerate(pick):
+        assert np.array_equal(idx[rp[q]:rp[q + 1]], idx0[rp0[j]:rp0[j + 1]])
+    assert (lat > 0).all()
