@@ -1,5 +1,5 @@
 // Batched queries: many pattern batches, each with its own k and metric,
-// answered by one pass of the pipeline (a8 of the build plan; the paper is
+// answered by one pass of the pipeline (the paper is
 // single-query, Sec. 4).  Batches that share (k, metric) form one group;
 // patterns are bucketed by (group, length), so every tile of the fused
 // filter + verify kernel has one k and one metric.

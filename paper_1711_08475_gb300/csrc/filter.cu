@@ -15,12 +15,15 @@
 // ceil(F_D / 2) <= k (Eq. 1).
 //
 // Passing pairs are rare (well under 1% on the English-like workloads) but a
-// warp tests 256 pairs per query, so most warp-steps still hold one.  The hot
+// warp tests 128 pairs per query, so most warp-steps still hold one.  The hot
 // loop therefore only records, per thread, a bit per query saying "one of my
-// fingerprints passed" (min over its F_D values, one compare); after every 32
-// queries each thread re-tests just the queries whose bit is set and appends
-// the passing pairs to a per-warp buffer in shared memory.  A full buffer is
-// flushed to the global survivor list with one atomic reservation per flush.
+// fingerprints passed" (min over its F_D values, one compare).  After every 32
+// queries the lanes append their (lane, query) hits to a warp queue, and the
+// warp re-tests the queue exactly in rounds of 32 (one hit per lane, the
+// owner's fingerprints fetched by shuffles), appending the passing pairs to a
+// per-warp buffer in shared memory.  The buffer is emptied before any round
+// whose passes might not fit, with one atomic reservation on the global
+// survivor list per flush (or, in the fused form, by verifying it in place).
 #include <cuda_fp16.h>
 
 #include "verify_core.cuh"

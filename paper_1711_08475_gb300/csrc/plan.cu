@@ -1,9 +1,9 @@
-// Query plans: the whole query pipeline on plan-owned device buffers,
-// captured once into a CUDA graph and replayed (a8 of the build plan).
+// Query plans: the batched pipeline of pipe.cuh on plan-owned device
+// buffers, captured once into a CUDA graph and replayed.
 //
-// A plan holds every buffer a batch of up to max_queries patterns
-// (max_chars bytes, max_batches batches) needs.  fp_plan_run copies the
-// inputs into the plan's buffers, then launches the pipeline:
+// A plan holds one arena sized for its largest run (max_queries patterns,
+// max_chars bytes, max_batches batches, 32 distinct (k, metric) groups).
+// fp_plan_run copies the inputs into it, then launches the pipeline:
 //   per-pattern group ids -> bucketing by (group, length) + fingerprints ->
 //   tile plan -> fused filter + verify (one persistent kernel over every
 //   batch and length bucket) -> sorted CSR -> counters to pinned memory.
