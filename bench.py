@@ -41,7 +41,7 @@ WORKLOAD = ("english1m: 1,000,000 English-like words (lognormal lengths mean 8, 
 def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fp", choices=["fp", "reference"])
     ap.add_argument("--words", type=int, default=1_000_000)
@@ -76,10 +76,14 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-lms", "200", "-i", str(self.device)],
+                                          "-lms", "50", "-i", str(self.device)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 3.0:  # sampling has started before the timed region
+                time.sleep(0.01)
+            self.lines.clear()
         except Exception:
             self.proc = None
         return self

@@ -142,3 +142,26 @@ def test_bounded_wait_and_errors(fp, served):
     want = alone(fp, pos, reqs[0].queries, 1, "ham")
     assert np.array_equal(r.csr()[1], want[1])
     srv.free()
+
+
+def test_empty_and_tiny_inputs(fp, served):
+    w, ix, reqs = served
+    S = datagen.Strings.from_list
+    # a plan run with no patterns, then with empty and one-byte patterns
+    plan = fp.Plan(ix, 8, 64, 2)
+    rp, idx = plan.run(S([]), batches=[(0, 1, "lev")]).csr()
+    assert list(rp) == [0] and len(idx) == 0
+    q = S([b"", b"a", b"", b"/"])
+    rp, idx = plan.run(q, batches=[(2, 1, "lev"), (2, 0, "ham")]).csr()
+    plan.free()
+    for lo, hi, k, m in ((0, 2, 1, "lev"), (2, 4, 0, "ham")):
+        rp0, idx0 = oracle.match(w.dictionary, q.subset(np.arange(lo, hi)), k, m)
+        assert np.array_equal(rp[lo:hi + 1] - rp[lo], rp0) and np.array_equal(idx[rp[lo]:rp[hi]], idx0)
+    # the server takes a request of empty and one-byte patterns
+    srv = fp.Server(ix, lanes=1)
+    got = srv.wait(srv.submit(q, k=1, metric="lev"), timeout_s=60).csr()
+    srv.free()
+    rp0, idx0 = oracle.match(w.dictionary, q, 1, "lev")
+    assert np.array_equal(got[0], rp0) and np.array_equal(got[1], idx0)
+    with pytest.raises(fp.FpError):
+        fp.Server(ix, lanes=1).submit(S([]), k=1, metric="lev")  # a request needs at least one pattern
