@@ -225,7 +225,7 @@ def filter_traffic():
     if not os.path.exists(prof):
         return None
     h = hashlib.sha256()
-    for f in ("filter.cu", "common.cuh", "verify_core.cuh"):
+    for f in ("filter.cu", "verify_core.cuh"):
         h.update(open(os.path.join(csrc, f), "rb").read())
     kv = dict(line.split(": ", 1) for line in open(prof).read().splitlines()
               if line.startswith(("source_hash: ", "bytes_per_launch: ")))
@@ -545,7 +545,7 @@ def main():
             for m in metrics:
                 r = fp.fp_query_ex(ix, pinned[m][0].numpy(), pinned[m][1].numpy(), k=1, metric=m,
                                     variant=args.variant)
-                rp, idx = r.csr()
+                rp, idx = r.csr(copy=False)
                 got += rp.nbytes + idx.nbytes
                 r.free()
             t1 = time.perf_counter()

@@ -71,17 +71,25 @@ class Result:
         self._h = handle
         self.n_queries = n_queries
 
-    def csr(self):
-        """Host copies: (row_ptr int64[n+1], idx int32[row_ptr[n]])."""
+    def csr(self, copy: bool = True):
+        """Host match lists: (row_ptr int64[n+1], idx int32[row_ptr[n]]).
+
+        copy=False returns views of the library's host buffers instead of
+        copies; they keep this result alive and stay valid until free()."""
         L = load()
         rp, ix = ctypes.c_void_p(), ctypes.c_void_p()
         check(L.fp_result_csr(self._h, ctypes.byref(rp), ctypes.byref(ix), 0), "fp_result_csr")
-        row_ptr = np.ctypeslib.as_array(ctypes.cast(rp, ctypes.POINTER(ctypes.c_int64)),
-                                        shape=(self.n_queries + 1,)).copy()
+        rbuf = (ctypes.c_int64 * (self.n_queries + 1)).from_address(rp.value)
+        rbuf._owner = self
+        row_ptr = np.frombuffer(rbuf, dtype=np.int64)
         n = int(row_ptr[-1])
-        idx = (np.ctypeslib.as_array(ctypes.cast(ix, ctypes.POINTER(ctypes.c_int32)), shape=(n,)).copy()
-               if n else np.zeros(0, np.int32))
-        return row_ptr, idx
+        if n:
+            ibuf = (ctypes.c_int32 * n).from_address(ix.value)
+            ibuf._owner = self
+            idx = np.frombuffer(ibuf, dtype=np.int32)
+        else:
+            idx = np.zeros(0, np.int32)
+        return (row_ptr.copy(), idx.copy()) if copy else (row_ptr, idx)
 
     def device_csr(self):
         """Device pointers (row_ptr, idx) owned by this result."""

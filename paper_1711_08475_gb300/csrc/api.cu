@@ -13,6 +13,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -144,6 +145,57 @@ static int stage_strings(const uint8_t *chars, const int64_t *off, int64_t n, cu
 
 using namespace fpk;
 
+
+namespace fpk {
+
+// Pinned host memory for copying match lists back: blocks are sized in powers
+// of two from 64 KB, and freed blocks are kept (up to 1 GB in total) for the
+// next result, so a result is copied at pinned-memory speed without a
+// cudaMallocHost per result.
+namespace {
+std::mutex g_pin_mu;
+std::vector<std::pair<size_t, void *>> g_pin_free;
+size_t g_pin_kept = 0;
+constexpr size_t PIN_KEEP = size_t(1) << 30;
+}  // namespace
+
+void *pinned_get(size_t bytes, size_t *cap) {
+    size_t c = size_t(1) << 16;
+    while (c < bytes) c <<= 1;
+    {
+        std::lock_guard<std::mutex> g(g_pin_mu);
+        for (size_t i = 0; i < g_pin_free.size(); i++)
+            if (g_pin_free[i].first == c) {
+                void *p = g_pin_free[i].second;
+                g_pin_free.erase(g_pin_free.begin() + (long)i);
+                g_pin_kept -= c;
+                *cap = c;
+                return p;
+            }
+    }
+    void *p = nullptr;
+    if (cudaMallocHost(&p, c) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    *cap = c;
+    return p;
+}
+
+void pinned_put(void *p, size_t cap) {
+    if (!p) return;
+    {
+        std::lock_guard<std::mutex> g(g_pin_mu);
+        if (g_pin_kept + cap <= PIN_KEEP) {
+            g_pin_free.emplace_back(cap, p);
+            g_pin_kept += cap;
+            return;
+        }
+    }
+    cudaFreeHost(p);
+}
+
+}  // namespace fpk
 
 extern "C" {
 
@@ -559,18 +611,39 @@ int fp_result_csr(fp_result *r, const int64_t **row_ptr, const int32_t **idx, in
         *idx = r->d_idx;
         return FP_OK;
     }
-    if (!r->host_ready) {
-        r->h_row_ptr.resize((size_t)r->n_queries + 1);
-        r->h_idx.resize((size_t)std::max<int64_t>(r->n_matches, 1));
-        FP_CUDA(cudaMemcpy(r->h_row_ptr.data(), r->d_row_ptr, sizeof(int64_t) * (size_t)(r->n_queries + 1),
-                           cudaMemcpyDeviceToHost));
-        if (r->n_matches > 0)
-            FP_CUDA(cudaMemcpy(r->h_idx.data(), r->d_idx, sizeof(int32_t) * (size_t)r->n_matches,
-                               cudaMemcpyDeviceToHost));
-        r->host_ready = true;
+    if (!r->host_ready && !r->pin) {
+        const size_t rb = sizeof(int64_t) * (size_t)(r->n_queries + 1);
+        const size_t ib = sizeof(int32_t) * (size_t)std::max<int64_t>(r->n_matches, 1);
+        size_t cap = 0;
+        void *p = pinned_get(rb + ib, &cap);
+        if (p) {  // one pinned block: row_ptr, then idx
+            cudaError_t e = cudaMemcpy(p, r->d_row_ptr, rb, cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess && r->n_matches > 0)
+                e = cudaMemcpy((uint8_t *)p + rb, r->d_idx, sizeof(int32_t) * (size_t)r->n_matches,
+                               cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) {
+                pinned_put(p, cap);
+                return cuda_fail(e, "fp_result_csr");
+            }
+            r->pin = p;
+            r->pin_cap = cap;
+        } else {  // no pinned memory to be had: ordinary host memory
+            r->h_row_ptr.resize((size_t)r->n_queries + 1);
+            r->h_idx.resize((size_t)std::max<int64_t>(r->n_matches, 1));
+            FP_CUDA(cudaMemcpy(r->h_row_ptr.data(), r->d_row_ptr, rb, cudaMemcpyDeviceToHost));
+            if (r->n_matches > 0)
+                FP_CUDA(cudaMemcpy(r->h_idx.data(), r->d_idx, sizeof(int32_t) * (size_t)r->n_matches,
+                                   cudaMemcpyDeviceToHost));
+            r->host_ready = true;
+        }
     }
-    *row_ptr = r->h_row_ptr.data();
-    *idx = r->h_idx.data();
+    if (r->pin) {
+        *row_ptr = (const int64_t *)r->pin;
+        *idx = (const int32_t *)((const uint8_t *)r->pin + sizeof(int64_t) * (size_t)(r->n_queries + 1));
+    } else {
+        *row_ptr = r->h_row_ptr.data();
+        *idx = r->h_idx.data();
+    }
     return FP_OK;
 }
 
@@ -586,6 +659,7 @@ void fp_result_free(fp_result *r) {
     // the release after all work on blocking streams
     if (r->d_row_ptr) cudaFreeAsync(r->d_row_ptr, 0);
     if (r->d_idx) cudaFreeAsync(r->d_idx, 0);
+    pinned_put(r->pin, r->pin_cap);
     delete r;
 }
 

@@ -200,8 +200,16 @@ struct fp_result {
     std::vector<int64_t> h_row_ptr;
     std::vector<int32_t> h_idx;
     bool host_ready = false;
+    void *pin = nullptr;  // pinned host copy: row_ptr then idx (from the pinned pool)
+    size_t pin_cap = 0;
     fp_stats stats{};
 };
+
+namespace fpk {
+// Pinned host blocks for result copies, reused across results.
+void *pinned_get(size_t bytes, size_t *cap);
+void pinned_put(void *p, size_t cap);
+}  // namespace fpk
 
 // The resident dictionary behind the opaque fp_index handle.
 struct fp_index {
