@@ -207,7 +207,7 @@ static __device__ __noinline__ bool verify_one(const FilterArgs &A, uint64_t e, 
     const uint8_t *da = A.d_str + (uint64_t)A.d_row16[ds] * 16;
     bool hit;  // k = 1 and 2 inline (the common cases), other k through the out-of-line switch
     if (metric == FP_HAM) hit = m == L && ham_within(qa, da, m, k);
-    else if (k == 1) hit = m - L <= 1 && L - m <= 1 && lev_within<1>(qa, m, da, L);
+    else if (k == 1) hit = lev1_within(qa, m, da, L);
     else if (k == 2) hit = m - L <= 2 && L - m <= 2 && lev_within<2>(qa, m, da, L);
     else hit = m - L <= k && L - m <= k && lev_within_k(k, qa, m, da, L);
     *key = ((uint64_t)(uint32_t)A.q_idx[qs] << A.idx_bits) | (uint64_t)(uint32_t)A.d_idx[ds];

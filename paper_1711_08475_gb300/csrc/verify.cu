@@ -23,6 +23,11 @@
 // column.  Every move keeps or increases i, so bits for rows beyond |A| never
 // reach row |A| and need no mask.  Lev(A, B) <= k iff bit |A| - |B| + k of
 // R_k is set after the last column; the scan stops early once R_k is empty.
+//
+// For k = 1 the recurrence is not needed: with equal lengths one edit is a
+// substitution (at most one differing byte), and with lengths differing by
+// one the shorter string is the longer one minus one byte, which one pass
+// over the first mismatch and the shifted suffix decides (lev1_within).
 #include "verify_core.cuh"
 
 namespace fpk {
@@ -132,7 +137,10 @@ __global__ void __launch_bounds__(256) k_verify(VerifyArgs A, int k) {
 #pragma unroll
             for (int u = 0; u < U; u++)
                 hit[u] = m[u] >= 0 && m[u] - L[u] <= K && L[u] - m[u] <= K &&
-                         lev_within<K>(A.q_str + (uint64_t)qr[u] * 16, m[u], A.d_str + (uint64_t)dr[u] * 16, L[u]);
+                         (K == 1 ? lev1_within(A.q_str + (uint64_t)qr[u] * 16, m[u], A.d_str + (uint64_t)dr[u] * 16,
+                                               L[u])
+                                 : lev_within<K>(A.q_str + (uint64_t)qr[u] * 16, m[u],
+                                                 A.d_str + (uint64_t)dr[u] * 16, L[u]));
         }
 #pragma unroll
         for (int u = 0; u < U; u++) {

@@ -39,6 +39,48 @@ __device__ __forceinline__ bool ham_within_first(uint4 x, uint4 y, const uint8_t
     return true;
 }
 
+// Bytes [lo, hi) of a little-endian 32-bit word, 0 <= lo <= hi <= 4.
+__device__ __forceinline__ uint32_t byte_range_mask(int lo, int hi) {
+    const uint32_t up = hi >= 4 ? 0xFFFFFFFFu : ((1u << (8 * hi)) - 1u);
+    const uint32_t low = lo <= 0 ? 0u : ((1u << (8 * lo)) - 1u);
+    return up & ~low;
+}
+
+// Lev(a, b) <= 1 without the strip DP.  Equal lengths: one edit can only be a
+// substitution, so Lev <= 1 iff at most one byte differs.  Lengths differing
+// by one: the shorter string must be the longer one with one byte deleted,
+// i.e. the two agree before their first mismatch p (p = the shorter length
+// if there is none) and the longer string's bytes after p equal the shorter
+// one's bytes from p on.  Strings sit in zero-padded 16-byte rows with
+// readable bytes after them; bytes outside a string are masked off.
+__device__ __forceinline__ bool lev1_within(const uint8_t *a, int m, const uint8_t *b, int n) {
+    if (m == n) return ham_within(a, b, m, 1);
+    if (m < n) {  // a is the longer one
+        const uint8_t *t = a;
+        a = b;
+        b = t;
+        const int u = m;
+        m = n;
+        n = u;
+    }
+    if (m != n + 1) return false;
+    const uint32_t *A = (const uint32_t *)a, *B = (const uint32_t *)b;
+    int p = n;  // first mismatch among bytes [0, n)
+    for (int j = 0; 4 * j < n; j++) {
+        const uint32_t x = (A[j] ^ B[j]) & byte_range_mask(0, n - 4 * j);
+        if (x) {
+            p = 4 * j + ((__ffs(x) - 1) >> 3);
+            break;
+        }
+    }
+    // a[i + 1] == b[i] for every i in [p, n)
+    for (int j = p >> 2; 4 * j < n; j++) {
+        const uint32_t shifted = __funnelshift_r(A[j], A[j + 1], 8);  // bytes 4j+1 .. 4j+4 of a
+        if ((shifted ^ B[j]) & byte_range_mask(p - 4 * j, n - 4 * j)) return false;
+    }
+    return true;
+}
+
 template <int K>
 __device__ __forceinline__ bool lev_within(const uint8_t *a, int m, const uint8_t *b, int n) {
     constexpr int BAND = 2 * K + 1;

@@ -473,3 +473,23 @@ def test_serving5m_full_sampled(fp):
     for j, q in enumerate(pick):
         assert np.array_equal(idx[rp[q]:rp[q + 1]], idx0[rp0[j]:rp0[j + 1]])
     assert (lat > 0).all()
+
+
+def test_levenshtein_one_exhaustive(fp):
+    """Every pair of strings over {a, b, c} up to length 4, plus longer strings
+    around the 4- and 16-byte word and row edges, at k = 1 and k = 0 (the
+    direct Lev <= 1 test and the strip recurrence must agree with the DP)."""
+    import itertools
+    small = [b""] + [bytes(t) for n in range(1, 5) for t in itertools.product(b"abc", repeat=n)]
+    law = datagen.StringLaw(np.frombuffer(b"ab", np.uint8), np.ones(2), datagen.LengthLaw("uniform", 14, 36))
+    long = law.draw(12, "edge", 300).to_list()
+    muts = datagen.make_queries(datagen.Strings.from_list(long), law, 12, "edge/q", 300, 1.0, "lev").to_list()
+    d = datagen.Strings.from_list(small + long)
+    q = datagen.Strings.from_list(small + muts)
+    for t, width in (("occ", 16), ("count", 32)):
+        ix = fp.fp_build(d, fp_type=t, width=width)
+        for k in (0, 1):
+            for mode in ("tiled", "fused"):
+                res = fp.fp_query_ex(ix, q, k=k, metric="lev", mode=mode)
+                rp0, idx0 = oracle.match(d, q, k, "lev")
+                assert_same(res, rp0, idx0, f"lev k={k} {t}{width} {mode}")
