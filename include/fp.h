@@ -113,6 +113,9 @@ typedef struct {
     float ms_verify;      /* Hamming / Levenshtein verification */
     float ms_emit;        /* sort and CSR */
     float ms_total;       /* whole call on the device, copy-in included */
+    int64_t pairs_tested; /* pairs the filter kernel tested: the eligible pairs less those whose
+                             fingerprint weights differ by more than 2k (rejected by Eq. 1
+                             without a test; see fp_build) */
 } fp_stats;
 
 typedef struct {
@@ -128,9 +131,14 @@ typedef struct fp_index fp_index;
 typedef struct fp_result fp_result;
 
 /* ---- build (Sec. 3.2 construction, Sec. 3.4 storage) -------------------- */
-/* Copies the dictionary to the device, buckets it by length (stable: within a
- * bucket words keep ascending index order), chooses the symbol map (Sec. 3
- * symbol sets) and builds one fingerprint per word (Sec. 3.2).
+/* Copies the dictionary to the device, buckets it by length, chooses the
+ * symbol map (Sec. 3 symbol sets) and builds one fingerprint per word
+ * (Sec. 3.2).  For occurrence, occurrence-halved and count fingerprints the
+ * words of a bucket are then ordered by fingerprint weight (population count;
+ * equal weights keep ascending index order) and the first word of every weight
+ * is recorded: since popc(a ^ b) >= |popc(a) - popc(b)|, a query tile tests
+ * only the words whose weight lies within 2k of its patterns' weights (Eq. 1
+ * rejects the rest).  Position fingerprints keep index order.
  *   chars, offsets: host or device; offsets[0] == 0, non-decreasing,
  *     n_words + 1 entries, every length <= 255.
  *   type: fp_type; width_bits: 16 or 32.

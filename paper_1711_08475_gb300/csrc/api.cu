@@ -269,6 +269,15 @@ int fp_build(const uint8_t *chars, const int64_t *offsets, int64_t n_words, int 
     }
     rc = bucketize(S.chars, S.off, n_words, S.total, nullptr, 1, ix->d_map, P, false, st, &ix->D, d_err);
     if (rc != FP_OK) goto fail_out;
+    if (P.type != FP_POS) {  // weight order of every bucket (population-count fingerprints)
+        if (cudaMalloc((void **)&ix->d_wstart, sizeof(int32_t) * 256 * (size_t)(cell_count(P.width) + 1)) !=
+            cudaSuccess) {
+            rc = cuda_fail(cudaGetLastError(), "weight table");
+            goto fail_out;
+        }
+        rc = weight_order(&ix->D, P, ix->d_wstart, st);
+        if (rc != FP_OK) goto fail_out;
+    }
     {
         cudaError_t e;
         if ((e = cudaMemcpyAsync(ix->h_count, ix->D.b_count, sizeof(ix->h_count), cudaMemcpyDeviceToHost, st)) !=
@@ -309,6 +318,7 @@ void fp_free(fp_index *ix) {
     free_bucketed(&ix->D, 0);
     if (ix->d_map) cudaFree(ix->d_map);
     if (ix->d_counts) cudaFree(ix->d_counts);
+    if (ix->d_wstart) cudaFree(ix->d_wstart);
     delete ix;
 }
 
@@ -341,6 +351,7 @@ int fp_set_symbol_map(fp_index *ix, const int8_t *map) {
     FP_CUDA(cudaMemcpy(ix->d_map, ix->h_map, 256, cudaMemcpyHostToDevice));
     ix->set = FP_SET_CUSTOM;
     FP_TRY(refingerprint(&ix->D, ix->d_map, ix->P, 0));
+    if (ix->d_wstart) FP_TRY(weight_order(&ix->D, ix->P, ix->d_wstart, 0));  // the weights changed with the map
     FP_CUDA(cudaDeviceSynchronize());
     return FP_OK;
 }
@@ -454,6 +465,7 @@ int fp_query_ex(fp_index *ix, const uint8_t *chars, const int64_t *offsets, int6
     const int q_bits = bits_for(n_queries), idx_bits = ix->idx_bits;
     int tq = 0, tw = 0;
     tile_shape(cfg, ix->P, &tq, &tw);
+    const bool band = ix->d_wstart != nullptr && o.mode != FP_MODE_PLAIN;
     int64_t pairs_bound;
     cudaError_t e;
 #define CK(call)                                 \
@@ -479,11 +491,21 @@ int fp_query_ex(fp_index *ix, const uint8_t *chars, const int64_t *offsets, int6
         CK(cudaMemcpyAsync(R.d_group, hg, 2 * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     }
     CK(cudaMemsetAsync(R.d_err, 0, sizeof(int32_t), st));
-    TRY(bucketize(S.chars, S.off, n_queries, S.total, nullptr, 1, ix->d_map, ix->P, true, st, &R.Q, R.d_err));
-    R.plan.max_segments = 256 * (2 * k + 1);
+    TRY(bucketize(S.chars, S.off, n_queries, S.total, nullptr, 1, ix->d_map, ix->P, true, st, &R.Q, R.d_err, band));
+    // weight bands: patterns in cell order; per tile of tq patterns and
+    // dictionary bucket at most one run of cells per high-half weight (the
+    // plain scan tests every pair)
+    if (band) {
+        R.plan.max_segments = (int)std::min<int64_t>(
+            0x7FFFFFFF, ((n_queries + tq - 1) / tq + 256) * (metric == FP_HAM ? 1 : 2 * k + 1) *
+                            cell_radix(ix->P.width));
+    } else {
+        R.plan.max_segments = 256 * (2 * k + 1);
+    }
     CK(cudaMallocAsync((void **)&R.plan.seg, sizeof(Segment) * (size_t)R.plan.max_segments, st));
     CK(cudaMallocAsync((void **)&R.plan.scal, 8 * sizeof(uint64_t), st));
-    TRY(plan_segments(R.Q, ix->D, R.d_group, R.d_group + 1, tq, tw, &R.plan, st));
+    TRY(plan_segments(R.Q, ix->D, R.d_group, R.d_group + 1, tq, tw, &R.plan, st, band ? ix->d_wstart : nullptr,
+                      ix->P.width));
     // survivor capacity: exact pair count when the host saw the lengths, else a bound
     if (S.host_checked) {
         pairs_bound = host_pairs(ix, S.host_len_hist, k, metric);
@@ -575,6 +597,7 @@ int fp_query_ex(fp_index *ix, const uint8_t *chars, const int64_t *offsets, int6
     }
     res->n_matches = (int64_t)scal[5];
     res->stats.pairs = (int64_t)scal[2];
+    res->stats.pairs_tested = (int64_t)scal[7];
     res->stats.survivors = (int64_t)scal[4];
     if (scal[2] > 0) ix->surv_ratio = std::max(1.0 / 4096.0, (double)scal[4] / (double)scal[2]);
     res->stats.matches = (int64_t)scal[5];

@@ -207,6 +207,44 @@ __global__ void k_bin_keys(const int64_t *__restrict__ off, int64_t n, const int
         if (h[t]) atomicAdd(&hist[t], h[t]);
 }
 
+
+constexpr int CELL_BITS = 9;  // cell_count(32) = 289 < 512
+
+// k_bin_keys with the weight cell of each string's fingerprint between the bin
+// and the index, so that the sort leaves every bin in cell order.
+template <int TYPE>
+__global__ void k_bin_keys_cells(const int64_t *__restrict__ off, const uint8_t *__restrict__ chars, int64_t n,
+                                 const int32_t *__restrict__ group, int nbins, const int8_t *__restrict__ map,
+                                 FpParams P, uint64_t *__restrict__ keys, int32_t *__restrict__ hist,
+                                 int32_t *__restrict__ err) {
+    extern __shared__ int32_t h[];
+    __shared__ int8_t smap[256];
+    for (int t = threadIdx.x; t < nbins; t += blockDim.x) h[t] = 0;
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) smap[t] = map[t];
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t L = off[i + 1] - off[i];
+        const int g = group ? group[i] : 0;
+        int bin = 0, cell = 0;
+        if (L < 0 || L > MAX_LEN || g < 0 || (int64_t)g * 256 + L >= nbins) {
+            atomicOr(err, 1);
+        } else {
+            bin = g * 256 + (int)L;
+            const uint8_t *src = chars + off[i];
+            FpAcc<TYPE> acc;
+            acc.init(P);
+            for (int pos = 0; pos < (int)L; pos++) acc.add(smap[src[pos]], pos, (int)L, P);
+            cell = fp_cell(acc.finish(P), P.width);
+        }
+        keys[i] = ((((uint64_t)bin << CELL_BITS) | (uint64_t)cell) << 32) | (uint64_t)i;
+        atomicAdd(&h[bin], 1);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nbins; t += blockDim.x)
+        if (h[t]) atomicAdd(&hist[t], h[t]);
+}
+
 // One block of 1024 threads: bucket starts (aligned), unaligned starts and
 // string-row bases.  tot[0] = slots, tot[1] = 16-byte row units.
 __global__ void __launch_bounds__(1024) k_plan_bins(const int32_t *__restrict__ hist, int nbins,
@@ -262,14 +300,15 @@ __global__ void __launch_bounds__(256) k_scatter_fp(const uint64_t *__restrict__
                                                     const int8_t *__restrict__ map, FpParams P,
                                                     const int32_t *__restrict__ b_start,
                                                     const int32_t *__restrict__ b_ustart,
-                                                    const int64_t *__restrict__ b_str16, Bucketed B) {
+                                                    const int64_t *__restrict__ b_str16, Bucketed B,
+                                                    int bin_shift) {
     __shared__ int8_t smap[256];
     for (int t = threadIdx.x; t < 256; t += blockDim.x) smap[t] = map[t];
     __syncthreads();
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
         uint64_t key = sorted[p];
-        int bin = (int)(key >> 32);
+        int bin = (int)(key >> (32 + bin_shift));
         int64_t i = (int64_t)(key & 0xffffffffu);
         int L = bin & 255;
         int64_t rank = p - b_ustart[bin];
@@ -387,10 +426,165 @@ static int dev_alloc(void **p, size_t bytes, bool so, cudaStream_t st) {
     return FP_OK;
 }
 
+// ---------------------------------------------------------------------------
+// weight order inside the buckets
+// ---------------------------------------------------------------------------
+// F_D is the Hamming weight of the XOR of two fingerprints (Sec. 3.3) for
+// occurrence, occurrence-halved and count fingerprints, and the weight of an
+// XOR is at least the difference of the two weights: |H(x) - H(y)| <=
+// H(x XOR y).  With the strings of every bucket ordered by fingerprint weight,
+// a tile of patterns with weights [wmin, wmax] can skip every word whose
+// weight lies outside [wmin - 2k, wmax + 2k]: Eq. 1 rejects all those pairs.
+// weight_order sorts the real slots of each bin by (weight, current slot)
+// and, on request, records per bin the first slot of every weight.
+
+// Counts one launch and returns its launch error as a status.
+static int launched(const char *name) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? FP_OK : cuda_fail(e, name);
+}
+
+__device__ __forceinline__ int slot_cell(const void *fp, int width, int64_t s) {
+    return fp_cell(width == 16 ? (uint32_t)((const uint16_t *)fp)[s] : ((const uint32_t *)fp)[s], width);
+}
+
+// U[c] = real slots of the bins before c (one block).
+__global__ void __launch_bounds__(1024) k_bin_prefix(const int32_t *__restrict__ count, int nbins,
+                                                     int64_t *__restrict__ U) {
+    __shared__ int64_t s[1024];
+    const int t = threadIdx.x, per = (nbins + 1023) / 1024;
+    const int lo = min(nbins, t * per), hi = min(nbins, lo + per);
+    int64_t a = 0;
+    for (int c = lo; c < hi; c++) a += count[c];
+    s[t] = a;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const int64_t v = t >= o ? s[t - o] : 0;
+        __syncthreads();
+        s[t] += v;
+        __syncthreads();
+    }
+    int64_t r = s[t] - a;
+    for (int c = lo; c < hi; c++) {
+        U[c] = r;
+        r += count[c];
+    }
+}
+
+// One block per bin: key (bin, cell, slot) of every real slot, written at
+// the bin's place in slot order.
+__global__ void __launch_bounds__(256) k_weight_keys(Bucketed B, int width, const int64_t *__restrict__ U,
+                                                     uint64_t *__restrict__ keys) {
+    const int c = blockIdx.x;
+    const int32_t start = B.b_start[c], count = B.b_count[c];
+    for (int i = threadIdx.x; i < count; i += blockDim.x) {
+        const int64_t slot = start + i;
+        const uint64_t w = (uint64_t)slot_cell(B.fp, width, slot);
+        keys[U[c] + i] = ((((uint64_t)c << CELL_BITS) | w) << 32) | (uint64_t)slot;
+    }
+}
+
+// Moves the slots into cell order: sorted key p of bin c goes to slot
+// b_start[c] + (p - U[c]); the old arrays are read from copies.
+__global__ void __launch_bounds__(256) k_weight_permute(const uint64_t *__restrict__ keys, int64_t n, Bucketed B,
+                                                        int width, const int64_t *__restrict__ U,
+                                                        const uint8_t *__restrict__ old_fp,
+                                                        const int32_t *__restrict__ old_idx,
+                                                        const uint8_t *__restrict__ old_len,
+                                                        const uint32_t *__restrict__ old_row16) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = keys[p];
+        const int c = (int)(key >> (32 + CELL_BITS));
+        const int64_t from = (int64_t)(key & 0xffffffffu);
+        const int64_t to = B.b_start[c] + (p - U[c]);
+        if (width == 16) ((uint16_t *)B.fp)[to] = ((const uint16_t *)old_fp)[from];
+        else ((uint32_t *)B.fp)[to] = ((const uint32_t *)old_fp)[from];
+        B.idx[to] = old_idx[from];
+        B.len[to] = old_len[from];
+        B.row16[to] = old_row16[from];
+    }
+}
+
+// wstart[c * (NC + 1) + w] = first slot of bin c whose cell is >= w (w = NC:
+// the end of the bin's real slots); one thread per (bin, cell).
+__global__ void k_weight_table(const uint64_t *__restrict__ keys, const int32_t *__restrict__ b_start,
+                               const int32_t *__restrict__ b_count, const int64_t *__restrict__ U, int nbins,
+                               int NC, int32_t *__restrict__ wstart) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)nbins * (NC + 1)) return;
+    const int c = (int)(t / (NC + 1)), w = (int)(t % (NC + 1));
+    int64_t lo = U[c], hi = U[c] + b_count[c];  // first key of the run with cell >= w
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if ((int)((keys[mid] >> 32) & ((1u << CELL_BITS) - 1u)) < w) lo = mid + 1;
+        else hi = mid;
+    }
+    wstart[t] = b_start[c] + (int32_t)(lo - U[c]);
+}
+
+int weight_order(Bucketed *B, const FpParams &P, int32_t *d_wstart, cudaStream_t st) {
+    if (P.type == FP_POS || B->n <= 0) {
+        if (d_wstart)
+            FP_CUDA(cudaMemsetAsync(d_wstart, 0, sizeof(int32_t) * (size_t)B->nbins * (cell_count(P.width) + 1), st));
+        return FP_OK;
+    }
+    const int nbins = B->nbins;
+    const int64_t n = B->n, ns = B->n_slots;
+    const size_t fpw = P.width == 16 ? 2 : 4;
+    int bin_bits = 1;
+    while ((1 << bin_bits) < nbins) bin_bits++;
+    int64_t *U = nullptr;
+    uint64_t *keys = nullptr, *tmp = nullptr, *sorted = nullptr;
+    uint8_t *old = nullptr;
+    int rc = FP_OK;
+    const size_t o_idx = ((size_t)ns * fpw + 255) & ~(size_t)255, o_len = o_idx + (((size_t)ns * 4 + 255) & ~(size_t)255),
+                 o_row = o_len + (((size_t)ns + 255) & ~(size_t)255), total = o_row + (size_t)ns * 4;
+    cudaError_t e;
+    if ((e = cudaMallocAsync((void **)&U, sizeof(int64_t) * (size_t)nbins, st)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&keys, sizeof(uint64_t) * (size_t)n, st)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&tmp, sizeof(uint64_t) * (size_t)n, st)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&old, total, st)) != cudaSuccess) {
+        rc = cuda_fail(e, "weight_order: scratch");
+    } else if ((e = cudaMemcpyAsync(old, B->fp, (size_t)ns * fpw, cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
+               (e = cudaMemcpyAsync(old + o_idx, B->idx, (size_t)ns * 4, cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
+               (e = cudaMemcpyAsync(old + o_len, B->len, (size_t)ns, cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
+               (e = cudaMemcpyAsync(old + o_row, B->row16, (size_t)ns * 4, cudaMemcpyDeviceToDevice, st)) !=
+                   cudaSuccess) {
+        rc = cuda_fail(e, "weight_order: copies");
+    } else {
+        k_bin_prefix<<<1, 1024, 0, st>>>(B->b_count, nbins, U);
+        if ((rc = launched("k_bin_prefix")) == FP_OK) {
+            k_weight_keys<<<nbins, 256, 0, st>>>(*B, P.width, U, keys);
+            rc = launched("k_weight_keys");
+        }
+        if (rc == FP_OK)
+            rc = radix_sort_u64(keys, tmp, nullptr, n, 32, 32 + CELL_BITS + bin_bits, st, &sorted);
+        if (rc == FP_OK) {
+            k_weight_permute<<<grid_for(n, 256, 8192), 256, 0, st>>>(sorted, n, *B, P.width, U, old,
+                                                                      (const int32_t *)(old + o_idx), old + o_len,
+                                                                      (const uint32_t *)(old + o_row));
+            rc = launched("k_weight_permute");
+        }
+        if (rc == FP_OK && d_wstart) {
+            const int64_t nt = (int64_t)nbins * (cell_count(P.width) + 1);
+            k_weight_table<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(sorted, B->b_start, B->b_count, U, nbins,
+                                                                        cell_count(P.width), d_wstart);
+            rc = launched("k_weight_table");
+        }
+    }
+    if (U) cudaFreeAsync(U, st);
+    if (keys) cudaFreeAsync(keys, st);
+    if (tmp) cudaFreeAsync(tmp, st);
+    if (old) cudaFreeAsync(old, st);
+    return rc;
+}
+
 int bucketize(const uint8_t *d_chars, const int64_t *d_off, int64_t n, int64_t total_chars,
               const int32_t *d_group, int32_t n_groups, const int8_t *d_map, const FpParams &P,
-              bool so, cudaStream_t st, Bucketed *out, int32_t *d_err) {
+              bool so, cudaStream_t st, Bucketed *out, int32_t *d_err, bool cells) {
     Bucketed B;
+    const int shift = cells && P.type != FP_POS ? CELL_BITS : 0;
     B.stream_ordered = so;
     B.n = n;
     B.nbins = 256 * (n_groups < 1 ? 1 : n_groups);
@@ -434,7 +628,16 @@ int bucketize(const uint8_t *d_chars, const int64_t *d_off, int64_t n, int64_t t
         }
         if (n > 0) {
             int g = grid_for(n, 256, 2048);
-            k_bin_keys<<<g, 256, nbins * sizeof(int32_t), st>>>(d_off, n, d_group, nbins, keys, hist, d_err);
+            const size_t sh = nbins * sizeof(int32_t);
+            if (shift == 0)
+                k_bin_keys<<<g, 256, sh, st>>>(d_off, n, d_group, nbins, keys, hist, d_err);
+            else if (P.type == FP_OCC)
+                k_bin_keys_cells<FP_OCC><<<g, 256, sh, st>>>(d_off, d_chars, n, d_group, nbins, d_map, P, keys, hist, d_err);
+            else if (P.type == FP_OCC_HALVED)
+                k_bin_keys_cells<FP_OCC_HALVED><<<g, 256, sh, st>>>(d_off, d_chars, n, d_group, nbins, d_map, P, keys, hist,
+                                                                    d_err);
+            else
+                k_bin_keys_cells<FP_COUNT><<<g, 256, sh, st>>>(d_off, d_chars, n, d_group, nbins, d_map, P, keys, hist, d_err);
             g_launches++;
             if ((e = cudaGetLastError()) != cudaSuccess) { rc = cuda_fail(e, "k_bin_keys"); goto fail; }
         }
@@ -445,21 +648,21 @@ int bucketize(const uint8_t *d_chars, const int64_t *d_off, int64_t n, int64_t t
             int bin_bits = 1;
             while ((1 << bin_bits) < nbins) bin_bits++;
             uint64_t *sorted = keys;
-            rc = radix_sort_u64(keys, keys2, nullptr, n, 32, 32 + bin_bits, st, &sorted);
+            rc = radix_sort_u64(keys, keys2, nullptr, n, 32, 32 + shift + bin_bits, st, &sorted);
             if (rc != FP_OK) goto fail;
             int g = grid_for(n, 256, 8192);
             switch (P.type) {
                 case FP_OCC:
-                    k_scatter_fp<FP_OCC><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B.b_start, ustart, str16, B);
+                    k_scatter_fp<FP_OCC><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B.b_start, ustart, str16, B, shift);
                     break;
                 case FP_OCC_HALVED:
-                    k_scatter_fp<FP_OCC_HALVED><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B.b_start, ustart, str16, B);
+                    k_scatter_fp<FP_OCC_HALVED><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B.b_start, ustart, str16, B, shift);
                     break;
                 case FP_COUNT:
-                    k_scatter_fp<FP_COUNT><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B.b_start, ustart, str16, B);
+                    k_scatter_fp<FP_COUNT><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B.b_start, ustart, str16, B, shift);
                     break;
                 default:
-                    k_scatter_fp<FP_POS><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B.b_start, ustart, str16, B);
+                    k_scatter_fp<FP_POS><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B.b_start, ustart, str16, B, shift);
                     break;
             }
             g_launches++;
@@ -538,16 +741,16 @@ int bucketize_into(const uint8_t *d_chars, const int64_t *d_off, int64_t n, int6
         int g = grid_for(n, 256, 8192);
         switch (P.type) {
             case FP_OCC:
-                k_scatter_fp<FP_OCC><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B->b_start, S.ustart, S.str16, *B);
+                k_scatter_fp<FP_OCC><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B->b_start, S.ustart, S.str16, *B, 0);
                 break;
             case FP_OCC_HALVED:
-                k_scatter_fp<FP_OCC_HALVED><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B->b_start, S.ustart, S.str16, *B);
+                k_scatter_fp<FP_OCC_HALVED><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B->b_start, S.ustart, S.str16, *B, 0);
                 break;
             case FP_COUNT:
-                k_scatter_fp<FP_COUNT><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B->b_start, S.ustart, S.str16, *B);
+                k_scatter_fp<FP_COUNT><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B->b_start, S.ustart, S.str16, *B, 0);
                 break;
             default:
-                k_scatter_fp<FP_POS><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B->b_start, S.ustart, S.str16, *B);
+                k_scatter_fp<FP_POS><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B->b_start, S.ustart, S.str16, *B, 0);
                 break;
         }
         FP_LAUNCHED("k_scatter_fp");

@@ -85,13 +85,31 @@ struct Bucketed {
 
 // Copies / bucketizes / fingerprints n strings.  chars and offsets are device
 // pointers.  total_chars = offsets[n].  bin of string i = group[i] * 256 + len
-// (group may be null).  map is a device int8[256].
+// (group may be null).  map is a device int8[256].  cells: order every bin by
+// weight cell (fp_cell, stable), as weight_order would; position fingerprints
+// keep index order.
 int bucketize(const uint8_t *d_chars, const int64_t *d_off, int64_t n, int64_t total_chars,
               const int32_t *d_group, int32_t n_groups, const int8_t *d_map, const FpParams &fp,
-              bool stream_ordered, cudaStream_t st, Bucketed *out, int32_t *d_err);
+              bool stream_ordered, cudaStream_t st, Bucketed *out, int32_t *d_err, bool cells = false);
 void free_bucketed(Bucketed *b, cudaStream_t st);
 // Rebuilds fingerprints of an existing bucketed set from its rows.
 int refingerprint(Bucketed *b, const int8_t *d_map, const FpParams &fp, cudaStream_t st);
+// Weight cells.  A fingerprint f of width W has the cell (x, y) = (popc of
+// its high W/2 bits, popc of its low W/2 bits), numbered x * (W/2 + 1) + y.
+// For two fingerprints |x - x'| + |y - y'| <= popc(f ^ f'), so a pair whose
+// cells lie more than 2k apart (L1) fails Eq. 1.
+__host__ __device__ constexpr int cell_radix(int width) { return width / 2 + 1; }
+__host__ __device__ constexpr int cell_count(int width) { return cell_radix(width) * cell_radix(width); }
+__device__ __forceinline__ int fp_cell(uint32_t f, int width) {
+    const int h = width / 2;
+    return __popc(f >> h) * (h + 1) + __popc(f & ((1u << h) - 1u));
+}
+// Orders the real slots of every bin by weight cell (stable), for occurrence,
+// occurrence-halved and count fingerprints (a no-op for position
+// fingerprints).  d_wstart (optional, nbins * (cell_count(W) + 1) int32):
+// per bin the first slot of every cell 0 .. cell_count(W) (the last: the end
+// of the bin's real slots).
+int weight_order(Bucketed *b, const FpParams &fp, int32_t *d_wstart, cudaStream_t st);
 
 // Symbol statistics (Sec. 3 symbol sets): byte counts and the field map.
 int symbol_map(const uint8_t *d_chars, int64_t total, int set, int sigma, int8_t *d_map,
@@ -122,7 +140,7 @@ struct QueryPlan {
     int32_t max_segments = 0;
     // device scalars (one small block)
     uint64_t *scal = nullptr;   // [0] n_segments [1] total tiles [2] pairs [3] tile counter
-                                // [4] survivors [5] matches [6..7] spare
+                                // [4] survivors [5] matches [6] plan overflow [7] pairs tested
 };
 
 struct FilterCfg {
@@ -133,8 +151,13 @@ struct FilterCfg {
     bool mma;      // popcount-type fingerprints: dot products of +-1 vectors on the tensor cores
 };
 
+// d_wstart (optional): the dictionary's cell table (weight_order); when
+// given, the patterns' bins must be in cell order too, and each tile of tq
+// patterns gets segments per dictionary bucket restricted to the cells
+// Eq. 1 can pass.  width: fingerprint width in bits.
 int plan_segments(const Bucketed &q, const Bucketed &d, const int32_t *d_group_k,
-                  const int32_t *d_group_metric, int tq, int tw, QueryPlan *plan, cudaStream_t st);
+                  const int32_t *d_group_metric, int tq, int tw, QueryPlan *plan, cudaStream_t st,
+                  const int32_t *d_wstart = nullptr, int width = 32);
 
 int launch_filter(const Bucketed &q, const Bucketed &d, const QueryPlan &plan, const FpParams &fp,
                   const FilterCfg &cfg, uint64_t *surv, int64_t surv_cap, cudaStream_t st,
@@ -219,6 +242,7 @@ struct fp_index {
     fpk::Bucketed D;
     int8_t *d_map = nullptr;
     int8_t h_map[256];
+    int32_t *d_wstart = nullptr;  // weight order of the buckets (null: position fingerprints, no weight bands)
     unsigned long long *d_counts = nullptr;
     int32_t h_count[256];
     int32_t h_start[256];

@@ -329,6 +329,7 @@ int fp_plan_run(fp_plan *p, const uint8_t *chars, const int64_t *offsets, int64_
         if ((int64_t)sc[5] <= P.match_cap) {
             res->n_matches = (int64_t)sc[5];
             res->stats.pairs = (int64_t)sc[2];
+            res->stats.pairs_tested = (int64_t)sc[7];
             res->stats.survivors = (int64_t)sc[4];
             res->stats.matches = (int64_t)sc[5];
             res->stats.filter_launches = 1;

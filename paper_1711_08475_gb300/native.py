@@ -51,7 +51,7 @@ class fp_stats(ctypes.Structure):
     _fields_ = [("n_queries", ctypes.c_int64), ("pairs", ctypes.c_int64), ("survivors", ctypes.c_int64),
                 ("matches", ctypes.c_int64), ("filter_launches", ctypes.c_int64),
                 ("ms_prepare", ctypes.c_float), ("ms_filter", ctypes.c_float), ("ms_verify", ctypes.c_float),
-                ("ms_emit", ctypes.c_float), ("ms_total", ctypes.c_float)]
+                ("ms_emit", ctypes.c_float), ("ms_total", ctypes.c_float), ("pairs_tested", ctypes.c_int64)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}

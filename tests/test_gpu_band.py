@@ -1,0 +1,168 @@
+"""Weight bands (needs a GPU).
+
+The buckets are ordered by weight cell (popc of the fingerprint's high half,
+popc of its low half) and every query tile tests only the runs of cells whose
+L1 distance to the tile's cells is at most 2k: the halves' weight differences
+add up to at most popc(a ^ b), so the skipped pairs fail Eq. 1 (pinned on the
+CPU in test_oracle_pins.py).  Here: the match lists and the survivor count
+stay the oracle's, and the number of pairs the filter tested equals the count
+of a plain re-statement of the band rule on the oracle's fingerprints.
+"""
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fp():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+    from paper_1711_08475_gb300 import build
+    build.build()
+    import paper_1711_08475_gb300 as m
+    return m
+
+
+def popc(x):
+    x = np.asarray(x, dtype=np.uint64)
+    return np.array([bin(int(v)).count("1") for v in x], dtype=np.int64)
+
+
+def cells(f, width):
+    h = width // 2
+    f = np.asarray(f, dtype=np.uint64)
+    return popc(f >> np.uint64(h)) * (h + 1) + popc(f & np.uint64((1 << h) - 1))
+
+
+def expected_tested(d, q, k, metric, m, t, width, tq):
+    """Pairs a banded plan tests.  Per length bin the patterns sorted by cell
+    are cut into tiles of tq; with (x1, y1), (x2, y2) the cells of a tile's
+    first and last pattern, its x range is [x1, x2] and its y range [y1, y2]
+    when x1 = x2, else everything.  In every dictionary bucket of an
+    admissible length and for every x' within 2k of the x range, the tile
+    tests the words of cells (x', y') with y' within the remaining distance of
+    the y range: one run of slots, started at the bucket's 8-slot boundary
+    below its first word; runs that then touch or overlap are merged."""
+    R = width // 2 + 1
+    H = R - 1
+    cq = cells(oracle.fingerprints(q, m, t, width), width)
+    cd = cells(oracle.fingerprints(d, m, t, width), width)
+    lq, ld = q.lengths(), d.lengths()
+    by_len = {L: np.sort(cd[ld == L]) for L in np.unique(ld)}
+    total = 0
+    for n in np.unique(lq):
+        cs = np.sort(cq[lq == n])
+        lens = [n] if metric == "ham" else range(max(0, n - k), min(255, n + k) + 1)
+        for s in range(0, len(cs), tq):
+            tile = cs[s:s + tq]
+            x1, x2 = int(tile[0]) // R, int(tile[-1]) // R
+            ya, yb = (int(tile[0]) % R, int(tile[-1]) % R) if x1 == x2 else (0, H)
+            for L in lens:
+                if L not in by_len:
+                    continue
+                b = by_len[L]
+                runs = []
+                for x in range(max(0, x1 - 2 * k), min(H, x2 + 2 * k) + 1):
+                    r = 2 * k - max(0, x1 - x, x - x2)
+                    ylo, yhi = max(0, ya - r), min(H, yb + r)
+                    first = int(np.searchsorted(b, x * R + ylo, side="left"))
+                    end = int(np.searchsorted(b, x * R + yhi + 1, side="left"))
+                    if end <= first:
+                        continue
+                    s8 = first & ~7
+                    if runs and s8 <= runs[-1][1]:
+                        runs[-1][1] = max(runs[-1][1], end)
+                    else:
+                        runs.append([s8, end])
+                total += len(tile) * sum(e - a for a, e in runs)
+    return total
+
+
+@pytest.mark.parametrize("t,width", [("occ", 32), ("count", 32), ("occ", 16), ("occh", 16)])
+@pytest.mark.parametrize("metric,k", [("ham", 1), ("lev", 1), ("lev", 2), ("ham", 0)])
+@pytest.mark.parametrize("tq", [256, 24])
+def test_band_counts_and_results(fp, t, width, metric, k, tq):
+    if metric == "lev" and t == "occh":
+        pytest.skip("occurrence-halved fingerprints bound only the Hamming distance")
+    w = datagen.english1m(20000, 1500)
+    d, q = w.dictionary, w.queries[metric]
+    ix = fp.fp_build(d, fp_type=t, width=width)
+    m = ix.symbol_map()
+    r = fp.fp_query_ex(ix, q, k=k, metric=metric, tile_queries=tq)
+    rp, idx = r.csr()
+    st = r.stats()
+    rp0, idx0 = oracle.match(d, q, k, metric)
+    assert np.array_equal(rp, rp0) and np.array_equal(idx, idx0)
+    _, _, pairs, surv = oracle.filter_match(d, q, k, metric, m, t, width, gray=True)
+    assert st["pairs"] == pairs and st["survivors"] == surv
+    assert st["pairs_tested"] == expected_tested(d, q, k, metric, m, t, width, tq)
+    assert st["pairs_tested"] < st["pairs"]
+
+
+def test_plain_scan_and_position_fingerprints_test_every_pair(fp):
+    w = datagen.english1m(20000, 800)
+    d, q = w.dictionary, w.queries["ham"]
+    ix = fp.fp_build(d, fp_type="occ", width=32)
+    st = fp.fp_query_ex(ix, q, k=1, metric="ham", mode="plain").stats()
+    assert st["pairs_tested"] == st["pairs"] > 0
+    ixp = fp.fp_build(d, fp_type="pos", width=32)
+    r = fp.fp_query_ex(ixp, q, k=1, metric="ham")
+    st = r.stats()
+    assert st["pairs_tested"] == st["pairs"] > 0
+    rp0, idx0 = oracle.match(d, q, 1, "ham")
+    rp, idx = r.csr()
+    assert np.array_equal(rp, rp0) and np.array_equal(idx, idx0)
+
+
+@pytest.mark.parametrize("mode,variant", [("fused", 0), ("tiled", 2), ("tiled", 1)])
+def test_band_other_forms(fp, mode, variant):
+    w = datagen.english1m(30000, 2000)
+    ix = fp.fp_build(w.dictionary, fp_type="count", width=32)
+    for metric, k in (("lev", 1), ("ham", 2), ("lev", 3)):
+        q = w.queries[metric]
+        r = fp.fp_query_ex(ix, q, k=k, metric=metric, mode=mode, variant=variant)
+        rp0, idx0 = oracle.match(w.dictionary, q, k, metric)
+        rp, idx = r.csr()
+        assert np.array_equal(rp, rp0) and np.array_equal(idx, idx0), (mode, variant, metric, k)
+        st = r.stats()
+        assert st["pairs_tested"] <= st["pairs"]
+
+
+def test_band_after_new_symbol_map(fp):
+    """A new map changes every weight: the index is re-ordered and its table rebuilt."""
+    w = datagen.english1m(20000, 1000)
+    d, q = w.dictionary, w.queries["lev"]
+    ix = fp.fp_build(d, fp_type="occ", width=16)
+    m2 = oracle.map_from_order(b"zyxwvutsrqponmlk")  # 16 fields, rarely used letters first
+    ix.set_symbol_map(m2)
+    r = fp.fp_query_ex(ix, q, k=1, metric="lev")
+    rp0, idx0 = oracle.match(d, q, 1, "lev")
+    rp, idx = r.csr()
+    assert np.array_equal(rp, rp0) and np.array_equal(idx, idx0)
+    st = r.stats()
+    assert st["pairs_tested"] == expected_tested(d, q, 1, "lev", ix.symbol_map(), "occ", 16, 256)
+    _, _, _, surv = oracle.filter_match(d, q, 1, "lev", ix.symbol_map(), "occ", 16, gray=True)
+    assert st["survivors"] == surv
+
+
+@pytest.mark.parametrize("metric", ["ham", "lev"])
+def test_band_at_scale(fp, metric):
+    """Bins with many tiles (8,000 patterns): the bands skip a large share of the pairs."""
+    w = datagen.english1m(50000, 8000)
+    d, q = w.dictionary, w.queries[metric]
+    ix = fp.fp_build(d, fp_type="count", width=32)
+    m = ix.symbol_map()
+    for tq in (256, 64):
+        r = fp.fp_query_ex(ix, q, k=1, metric=metric, tile_queries=tq)
+        st = r.stats()
+        rp0, idx0 = oracle.match(d, q, 1, metric)
+        rp, idx = r.csr()
+        assert np.array_equal(rp, rp0) and np.array_equal(idx, idx0)
+        assert st["pairs_tested"] == expected_tested(d, q, 1, metric, m, "count", 32, tq)
+        assert st["pairs_tested"] < 0.95 * st["pairs"]

@@ -40,3 +40,23 @@ def test_filter_is_pure_speedup_uniform10k(orc):
         assert pairs == oracle.eligible_pairs(w.dictionary, Q, 1, metric)
         # the mutated half of the queries come from dictionary words within one edit
         assert (np.diff(rp0) > 0).sum() >= 450
+
+
+def test_weight_difference_bounds_fd(orc):
+    """popc(a ^ b) >= |popc(a) - popc(b)| on the oracle's own fingerprints, so a
+    pair whose weights differ by more than 2k fails Eq. 1; the GPU path skips
+    such pairs by weight-ordering its buckets."""
+    w = datagen.english1m(3000, 400)
+    for t, width in (("occ", 32), ("count", 32), ("occ", 16), ("occh", 16)):
+        m, _, _ = orc.symbol_map(w.dictionary.chars, "common", oracle.layout(t, width)["sigma"])
+        a = orc.fingerprints(w.dictionary, m, t, width).astype(np.uint64)
+        b = orc.fingerprints(w.queries["ham"], m, t, width).astype(np.uint64)
+        pa = np.array([bin(int(x)).count("1") for x in a])
+        pb = np.array([bin(int(x)).count("1") for x in b])
+        x = a[None, :] ^ b[:, None]
+        fdx = np.zeros(x.shape, dtype=np.int64)
+        for s in range(32):
+            fdx += ((x >> np.uint64(s)) & np.uint64(1)).astype(np.int64)
+        dw = np.abs(pa[None, :] - pb[:, None])
+        assert (fdx >= dw).all()
+        assert (fdx == dw).any() and (fdx > dw).any()  # both cases occur
