@@ -91,7 +91,8 @@ typedef enum {
 
 typedef struct {
     int32_t mode;            /* fp_mode; default FP_MODE_TILED */
-    int32_t tile_queries;    /* queries per block for FP_MODE_TILED / FUSED; 0 = autotuned / default */
+    int32_t tile_queries;    /* queries per block for FP_MODE_TILED / FUSED, 1..256; 0 = default (128 with
+                                weight bands, i.e. all but position fingerprints; 256 for those) */
     int32_t words_per_thread;/* dictionary fingerprints per thread per tile, 4 or 8; 0 = default */
     int32_t variant;         /* 0 = automatic (k = 1: a quarter of the pair tests use an ALU-only
                                 "at most two bits" test, identical decisions); 1 = population count only;

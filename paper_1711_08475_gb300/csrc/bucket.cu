@@ -712,8 +712,9 @@ namespace fpk {
 // 256 * n_groups bins) with the temporaries in S; allocates nothing.
 int bucketize_into(const uint8_t *d_chars, const int64_t *d_off, int64_t n, int64_t total_chars,
                    const int32_t *d_group, int32_t n_groups, const int8_t *d_map, const FpParams &P, cudaStream_t st,
-                   Bucketed *B, const BucketScratch &S, int32_t *d_err) {
+                   Bucketed *B, const BucketScratch &S, int32_t *d_err, bool cells) {
     const int nbins = 256 * (n_groups < 1 ? 1 : n_groups);
+    const int shift = cells && P.type != FP_POS ? CELL_BITS : 0;
     const int64_t slots_ub = n + (int64_t)(SLOT_ALIGN - 1) * nbins;
     const int64_t str_ub = total_chars + 15 * n;
     const size_t fpw = P.width == 16 ? 2 : 4;
@@ -728,7 +729,16 @@ int bucketize_into(const uint8_t *d_chars, const int64_t *d_off, int64_t n, int6
     FP_CUDA(cudaMemsetAsync(S.hist, 0, nbins * 4, st));
     if (n > 0) {
         const int g = grid_for(n, 256, 2048);
-        k_bin_keys<<<g, 256, nbins * sizeof(int32_t), st>>>(d_off, n, d_group, nbins, S.keys, S.hist, d_err);
+        const size_t sh = nbins * sizeof(int32_t);
+        if (shift == 0)
+            k_bin_keys<<<g, 256, sh, st>>>(d_off, n, d_group, nbins, S.keys, S.hist, d_err);
+        else if (P.type == FP_OCC)
+            k_bin_keys_cells<FP_OCC><<<g, 256, sh, st>>>(d_off, d_chars, n, d_group, nbins, d_map, P, S.keys, S.hist, d_err);
+        else if (P.type == FP_OCC_HALVED)
+            k_bin_keys_cells<FP_OCC_HALVED><<<g, 256, sh, st>>>(d_off, d_chars, n, d_group, nbins, d_map, P, S.keys, S.hist,
+                                                                d_err);
+        else
+            k_bin_keys_cells<FP_COUNT><<<g, 256, sh, st>>>(d_off, d_chars, n, d_group, nbins, d_map, P, S.keys, S.hist, d_err);
         FP_LAUNCHED("k_bin_keys");
     }
     k_plan_bins<<<1, 1024, 0, st>>>(S.hist, nbins, B->b_start, B->b_count, S.ustart, S.str16, S.tot);
@@ -737,20 +747,20 @@ int bucketize_into(const uint8_t *d_chars, const int64_t *d_off, int64_t n, int6
         int bin_bits = 1;
         while ((1 << bin_bits) < nbins) bin_bits++;
         uint64_t *sorted = S.keys;
-        FP_TRY(radix_sort_u64_into(S.keys, S.keys2, S.radix_hist, nullptr, n, 32, 32 + bin_bits, st, &sorted));
+        FP_TRY(radix_sort_u64_into(S.keys, S.keys2, S.radix_hist, nullptr, n, 32, 32 + shift + bin_bits, st, &sorted));
         int g = grid_for(n, 256, 8192);
         switch (P.type) {
             case FP_OCC:
-                k_scatter_fp<FP_OCC><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B->b_start, S.ustart, S.str16, *B, 0);
+                k_scatter_fp<FP_OCC><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B->b_start, S.ustart, S.str16, *B, shift);
                 break;
             case FP_OCC_HALVED:
-                k_scatter_fp<FP_OCC_HALVED><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B->b_start, S.ustart, S.str16, *B, 0);
+                k_scatter_fp<FP_OCC_HALVED><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B->b_start, S.ustart, S.str16, *B, shift);
                 break;
             case FP_COUNT:
-                k_scatter_fp<FP_COUNT><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B->b_start, S.ustart, S.str16, *B, 0);
+                k_scatter_fp<FP_COUNT><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B->b_start, S.ustart, S.str16, *B, shift);
                 break;
             default:
-                k_scatter_fp<FP_POS><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B->b_start, S.ustart, S.str16, *B, 0);
+                k_scatter_fp<FP_POS><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B->b_start, S.ustart, S.str16, *B, shift);
                 break;
         }
         FP_LAUNCHED("k_scatter_fp");

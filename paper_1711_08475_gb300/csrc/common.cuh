@@ -206,7 +206,7 @@ int build_csr_into(uint64_t *keys, uint64_t *tmp, uint32_t *hist, const uint64_t
                    int idx_bits, int64_t n_queries, int64_t *row_ptr, int32_t *idx, cudaStream_t st);
 int bucketize_into(const uint8_t *d_chars, const int64_t *d_off, int64_t n, int64_t total_chars,
                    const int32_t *d_group, int32_t n_groups, const int8_t *d_map, const FpParams &P, cudaStream_t st,
-                   Bucketed *B, const BucketScratch &S, int32_t *d_err);
+                   Bucketed *B, const BucketScratch &S, int32_t *d_err, bool cells = false);
 // group[i] = batch_group[b] for every pattern i of batch b (batch b covers
 // [batch_start[b], batch_start[b+1]), device arrays).
 int fill_groups(const int64_t *d_batch_start, const int32_t *d_batch_group, int n_batches, int32_t *d_group,

@@ -188,68 +188,81 @@ __global__ void __launch_bounds__(1024) k_plan_segments(
     __shared__ uint64_t s_t[1024];
     __shared__ unsigned long long s_pairs, s_tested;
     const int t = threadIdx.x;
-    const bool band = q_fp != nullptr && d_wstart != nullptr;
+    // a banded plan that does not fit falls back to whole buckets (which fit
+    // whenever max_segments >= bins x (2k + 1))
+    bool band = q_fp != nullptr && d_wstart != nullptr;
     const int nbins = min(q_nbins, PLAN_MAX_BINS);
-    if (t == 0) {
-        s_pairs = 0;
-        s_tested = 0;
-    }
-    // units per bin and their prefix
-    {
-        const int per = (nbins + 1023) / 1024;
-        const int lo = min(nbins, t * per), hi = min(nbins, lo + per);
-        int64_t a = 0;
-        for (int c = lo; c < hi; c++) a += plan_units(qb_count[c], band, tq);
-        s_t[t] = (uint64_t)a;
+    bool too_many = false;
+    int64_t u0 = 0, u1 = 0;
+    int c0 = 0;
+    PlanCounts pc;
+    for (;;) {
+        if (t == 0) {
+            s_pairs = 0;
+            s_tested = 0;
+        }
+        // units per bin and their prefix
+        {
+            const int per = (nbins + 1023) / 1024;
+            const int lo = min(nbins, t * per), hi = min(nbins, lo + per);
+            int64_t a = 0;
+            for (int c = lo; c < hi; c++) a += plan_units(qb_count[c], band, tq);
+            s_t[t] = (uint64_t)a;
+            __syncthreads();
+            for (int o = 1; o < 1024; o <<= 1) {
+                const uint64_t v = t >= o ? s_t[t - o] : 0;
+                __syncthreads();
+                s_t[t] += v;
+                __syncthreads();
+            }
+            int64_t r = (int64_t)s_t[t] - a;
+            for (int c = lo; c < hi; c++) {
+                s_unit0[c] = (int32_t)(r < 0x7FFFFFFF ? r : 0x7FFFFFFF);
+                r += plan_units(qb_count[c], band, tq);
+            }
+            if (t == 1023) s_unit0[nbins] = (int32_t)(s_t[1023] < 0x7FFFFFFFull ? s_t[1023] : 0x7FFFFFFFull);
+            __syncthreads();
+        }
+        too_many = s_t[1023] >= 0x7FFFFFFFull;  // units beyond int32: refuse the plan
+        const int64_t U = too_many ? 0 : s_unit0[nbins];
+        u0 = U * t / 1024;
+        u1 = U * (t + 1) / 1024;
+        {  // bin of unit u0: last bin whose first unit is <= u0
+            int lo = 0, hi = nbins - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_unit0[mid] <= u0) lo = mid;
+                else hi = mid - 1;
+            }
+            c0 = lo;
+        }
+        pc = PlanCounts{};
+        int64_t si = 0;
+        uint64_t tb = 0;
+        for (int64_t u = u0, c = c0; u < u1; u++) {
+            while (s_unit0[c + 1] <= u) c++;
+            plan_unit<false>((int)c, u - s_unit0[c], qb_start, qb_count, db_start, db_count, group_k, group_metric,
+                             tq, tw, q_fp, width, d_wstart, band, seg, max_segments, si, tb, pc);
+        }
+        s_n[t] = pc.nseg;
+        s_t[t] = pc.tiles;
+        atomicAdd(&s_pairs, (unsigned long long)pc.pairs);
+        atomicAdd(&s_tested, (unsigned long long)pc.tested);
         __syncthreads();
         for (int o = 1; o < 1024; o <<= 1) {
-            const uint64_t v = t >= o ? s_t[t - o] : 0;
+            const int32_t a = t >= o ? s_n[t - o] : 0;
+            const uint64_t b = t >= o ? s_t[t - o] : 0;
             __syncthreads();
-            s_t[t] += v;
+            s_n[t] += a;
+            s_t[t] += b;
             __syncthreads();
         }
-        int64_t r = (int64_t)s_t[t] - a;
-        for (int c = lo; c < hi; c++) {
-            s_unit0[c] = (int32_t)(r < 0x7FFFFFFF ? r : 0x7FFFFFFF);
-            r += plan_units(qb_count[c], band, tq);
-        }
-        if (t == 1023) s_unit0[nbins] = (int32_t)(s_t[1023] < 0x7FFFFFFFull ? s_t[1023] : 0x7FFFFFFFull);
-        __syncthreads();
+        if (!(band && s_n[1023] > max_segments)) break;
+        band = false;
+        __syncthreads();  // everyone has read s_n[1023] before it is reused
     }
-    const bool too_many = s_t[1023] >= 0x7FFFFFFFull;  // units beyond int32: refuse the plan
-    const int64_t U = too_many ? 0 : s_unit0[nbins];
-    const int64_t u0 = U * t / 1024, u1 = U * (t + 1) / 1024;
-    int c0 = 0;  // bin of unit u0: last bin whose first unit is <= u0
-    {
-        int lo = 0, hi = nbins - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (s_unit0[mid] <= u0) lo = mid;
-            else hi = mid - 1;
-        }
-        c0 = lo;
-    }
-    PlanCounts pc;
-    int64_t si = 0;
-    uint64_t tb = 0;
-    for (int64_t u = u0, c = c0; u < u1; u++) {
-        while (s_unit0[c + 1] <= u) c++;
-        plan_unit<false>((int)c, u - s_unit0[c], qb_start, qb_count, db_start, db_count, group_k, group_metric, tq,
-                         tw, q_fp, width, d_wstart, band, seg, max_segments, si, tb, pc);
-    }
-    s_n[t] = pc.nseg;
-    s_t[t] = pc.tiles;
-    atomicAdd(&s_pairs, (unsigned long long)pc.pairs);
-    atomicAdd(&s_tested, (unsigned long long)pc.tested);
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        const int32_t a = t >= o ? s_n[t - o] : 0;
-        const uint64_t b = t >= o ? s_t[t - o] : 0;
-        __syncthreads();
-        s_n[t] += a;
-        s_t[t] += b;
-        __syncthreads();
-    }
+    int64_t si;
+    uint64_t tb;
     si = (int64_t)s_n[t] - pc.nseg;
     tb = s_t[t] - pc.tiles;
     PlanCounts again;
@@ -387,6 +400,22 @@ __device__ __forceinline__ int find_segment(const Segment *seg, int nseg, uint64
         int mid = (lo + hi + 1) >> 1;
         if (seg[mid].tile_begin <= tile) lo = mid;
         else hi = mid - 1;
+    }
+    return lo;
+}
+
+// The same search by a whole warp, 32 probes per step (three dependent loads
+// for 32,768 segments instead of fifteen): the segment of `tile` is the last
+// one whose tile_begin <= tile; segment 0 begins at tile 0.
+__device__ __forceinline__ int find_segment_warp(const Segment *seg, int nseg, uint64_t tile, int lane) {
+    int lo = 0, hi = nseg;  // the answer lies in [lo, hi); seg[lo].tile_begin <= tile
+    while (hi - lo > 1) {
+        const int step = (hi - lo + 31) >> 5;
+        const int i = lo + lane * step;
+        const bool le = i < hi && seg[i].tile_begin <= tile;
+        const unsigned m = __ballot_sync(0xffffffffu, le);  // lane 0 always set
+        lo += (31 - __clz(m)) * step;
+        hi = min(hi, lo + step);
     }
     return lo;
 }
@@ -704,7 +733,7 @@ __global__ void __launch_bounds__(FT_THREADS, (ft_min_blocks<W, V, POS, FUSED>()
         __syncthreads();
         const uint64_t tile = s_tile;
         if (tile >= ntiles) break;
-        const Segment S = A.seg[find_segment(A.seg, nseg, tile)];
+        const Segment S = A.seg[find_segment_warp(A.seg, nseg, tile, lane)];
         const uint64_t local = tile - S.tile_begin;
         const uint32_t qt = (uint32_t)(local / S.n_dtiles), dt = (uint32_t)(local % S.n_dtiles);
         const uint32_t q0 = S.q_start + qt * (uint32_t)A.tq;
@@ -717,18 +746,28 @@ __global__ void __launch_bounds__(FT_THREADS, (ft_min_blocks<W, V, POS, FUSED>()
             s_q[j] = (W == 32) ? f : (f | (f << 16));
         }
         __syncthreads();
+        // A short tile (the end of a run of weight cells) has fingerprints for
+        // nch < 8 warps' columns; the block then splits its patterns into
+        // 8 / nchp slices (nchp: nch rounded up to a power of two) and warp
+        // (c, s) scans column c against slice s, so that no warp idles
+        // while there is work.
+        const uint32_t nch = min((nw + 32u * G - 1u) / (32u * G), (uint32_t)FT_WARPS);
+        const uint32_t nchp = nch <= 1u ? 1u : (nch <= 2u ? 2u : (nch <= 4u ? 4u : 8u));
+        const uint32_t col = (uint32_t)warp % nchp, slice = (uint32_t)warp / nchp, nsl = FT_WARPS / nchp;
+        const uint32_t qs = (((nq + nsl - 1u) / nsl) + 31u) & ~31u;  // whole batches of 32 patterns
+        const uint32_t qa = min(slice * qs, nq), qn = min(qs, nq - qa);
         // the thread's dictionary fingerprints, as 32-bit words
         uint32_t w[V];
         const uint32_t word0 = (W == 32) ? w0 : w0 / 2;  // w0 is a multiple of 8 slots
 #pragma unroll
         for (int r = 0; r < V / 4; r++) {
-            const uint4 x = *reinterpret_cast<const uint4 *>(A.dfp + word0 + r * (FT_THREADS * 4) + threadIdx.x * 4);
+            const uint4 x = *reinterpret_cast<const uint4 *>(A.dfp + word0 + r * (FT_THREADS * 4) + (col * 32u + lane) * 4);
             w[4 * r + 0] = x.x;
             w[4 * r + 1] = x.y;
             w[4 * r + 2] = x.z;
             w[4 * r + 3] = x.w;
         }
-        const uint32_t wrel = (uint32_t)warp * 32u * G;
+        const uint32_t wrel = col * 32u * G;
         const uint32_t wbase = w0 + wrel;
         const uint32_t nvalid = nw > wrel ? nw - wrel : 0u;
         // fingerprints past the tile end must never pass
@@ -736,20 +775,20 @@ __global__ void __launch_bounds__(FT_THREADS, (ft_min_blocks<W, V, POS, FUSED>()
 #pragma unroll
         for (int i = 0; i < NF; i++)
             if (lane_offset<G>(i, lane) >= nvalid) invalid |= 1u << i;
-        if (nvalid == 0u) {
-            // a short tile (a run of weight cells): this warp has no fingerprints
+        if (nvalid == 0u || qn == 0u) {
+            // nothing for this warp in a short tile
         } else if (K1MIX && T != 2u) {  // a k = 1 variant given another k: exact general path
             if (nw == (uint32_t)TW)
-                scan_tile<W, V, POS, true, false, FUSED>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, queue, qcnt, lane,
+                scan_tile<W, V, POS, true, false, FUSED>(A, s_q + qa, qn, q0 + qa, w, invalid, T, wbase, stage, cnt, queue, qcnt, lane,
                                                            S.k, S.metric);
             else
-                scan_tile<W, V, POS, false, false, FUSED>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, queue, qcnt, lane,
+                scan_tile<W, V, POS, false, false, FUSED>(A, s_q + qa, qn, q0 + qa, w, invalid, T, wbase, stage, cnt, queue, qcnt, lane,
                                                            S.k, S.metric);
         } else if (nw == (uint32_t)TW) {
-            scan_tile<W, V, POS, true, K1MIX, FUSED>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, queue, qcnt, lane,
+            scan_tile<W, V, POS, true, K1MIX, FUSED>(A, s_q + qa, qn, q0 + qa, w, invalid, T, wbase, stage, cnt, queue, qcnt, lane,
                                                            S.k, S.metric);
         } else {
-            scan_tile<W, V, POS, false, K1MIX, FUSED>(A, s_q, nq, q0, w, invalid, T, wbase, stage, cnt, queue, qcnt, lane,
+            scan_tile<W, V, POS, false, K1MIX, FUSED>(A, s_q + qa, qn, q0 + qa, w, invalid, T, wbase, stage, cnt, queue, qcnt, lane,
                                                            S.k, S.metric);
         }
         // fused: the next tile may have another (k, metric), so verify what is staged

@@ -36,6 +36,7 @@ struct Pipe {
     Bucketed Q;
     BucketScratch S{};
     QueryPlan qp;
+    int32_t seg_cap = 0;  // segments the arena holds
     int32_t *d_err = nullptr;
     int64_t match_cap = 0;
     uint64_t *matches = nullptr, *tmp = nullptr;

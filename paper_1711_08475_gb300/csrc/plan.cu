@@ -58,6 +58,10 @@ size_t pipe_layout(const PipeShape &s, uint8_t *base, Pipe *p) {
     const int64_t strb = s.chars + 15 * n + STR_SLACK;
     const int64_t cap = std::max<int64_t>(s.match_cap, 1);
     const int64_t rh = 256 * (int64_t)std::max(radix_blocks(cap), radix_blocks(n));
+    // segments: whole buckets need bins x 31 at most; weight bands about 18 per
+    // tile of 64 patterns (three lengths, a few runs of cells each) -- a plan
+    // that needs more falls back to whole buckets on the device
+    const int64_t seg_cap = std::min<int64_t>(0x7FFFFFFF, std::max<int64_t>(nbins * 31, (n / 64 + nbins) * 18));
     size_t off = 0;
     const size_t o_chars = carve(off, (size_t)s.chars + 16), o_off = carve(off, 8 * (size_t)(n + 1)),
                  o_bs = carve(off, 8 * (size_t)(s.batches + 1)), o_bg = carve(off, 4 * (size_t)s.batches),
@@ -68,7 +72,7 @@ size_t pipe_layout(const PipeShape &s, uint8_t *base, Pipe *p) {
                  o_bct = carve(off, 4 * (size_t)nbins), o_k1 = carve(off, 8 * (size_t)n),
                  o_k2 = carve(off, 8 * (size_t)n), o_hist = carve(off, 4 * (size_t)nbins),
                  o_ust = carve(off, 4 * (size_t)nbins), o_s16 = carve(off, 8 * (size_t)nbins),
-                 o_tot = carve(off, 16), o_seg = carve(off, sizeof(Segment) * (size_t)nbins * 31),
+                 o_tot = carve(off, 16), o_seg = carve(off, sizeof(Segment) * (size_t)seg_cap),
                  o_scal = carve(off, 8 * 8), o_err = carve(off, 4), o_row = carve(off, 8 * (size_t)(n + 1)),
                  o_m = carve(off, 8 * (size_t)cap), o_t = carve(off, 8 * (size_t)cap),
                  o_idx = carve(off, 4 * (size_t)cap), o_rh = carve(off, 4 * (size_t)rh);
@@ -95,6 +99,7 @@ size_t pipe_layout(const PipeShape &s, uint8_t *base, Pipe *p) {
         p->S.tot = (int64_t *)(base + o_tot);
         p->S.radix_hist = (uint32_t *)(base + o_rh);
         p->qp.seg = (Segment *)(base + o_seg);
+        p->seg_cap = (int32_t)seg_cap;
         p->qp.scal = (uint64_t *)(base + o_scal);
         p->d_err = (int32_t *)(base + o_err);
         p->row_ptr = (int64_t *)(base + o_row);
@@ -141,12 +146,16 @@ int pipe_enqueue(fp_index *ix, const FilterCfg &cfg, Pipe &p, int64_t n, int64_t
     if (ev) FP_CUDA(cudaEventRecord(ev[0], st));
     FP_CUDA(cudaMemsetAsync(p.d_err, 0, sizeof(int32_t), st));
     FP_TRY(fill_groups(p.d_batch_start, p.d_batch_group, n_batches, p.d_group, st));
+    // weight bands whenever the index has its cell table (not for position
+    // fingerprints): patterns in cell order, tiles restricted to runs of cells
+    const bool band = ix->d_wstart != nullptr;
     FP_TRY(bucketize_into(p.d_chars, p.d_off, n, total, p.d_group, n_groups, ix->d_map, ix->P, st, &p.Q, p.S,
-                          p.d_err));
-    p.qp.max_segments = nbins * 31;
+                          p.d_err, band));
+    p.qp.max_segments = p.seg_cap;
     int tq = 0, tw = 0;
     tile_shape(cfg, ix->P, &tq, &tw);
-    FP_TRY(plan_segments(p.Q, ix->D, p.d_group_km, p.d_group_km + MAX_GROUPS, tq, tw, &p.qp, st));
+    FP_TRY(plan_segments(p.Q, ix->D, p.d_group_km, p.d_group_km + MAX_GROUPS, tq, tw, &p.qp, st,
+                         band ? ix->d_wstart : nullptr, ix->P.width));
     if (ev) FP_CUDA(cudaEventRecord(ev[1], st));
     FP_TRY(launch_fused(p.Q, ix->D, p.qp, ix->P, cfg, ix->idx_bits, p.matches, p.match_cap, st, nullptr));
     if (ev) FP_CUDA(cudaEventRecord(ev[2], st));
