@@ -60,242 +60,6 @@ constexpr int FT_QUEUE = 256;  // queued (lane, tile query) hits per warp
 #define FT_UNROLL_PRAGMA(n) _Pragma(FT_STR(unroll n))
 
 // ---------------------------------------------------------------------------
-// tile planner: one block
-// ---------------------------------------------------------------------------
-// Without weight bands a segment is (query bin, dictionary bucket) with
-// ceil(q/tq) x ceil(d/tw) tiles.  With weight bands the patterns of every
-// bin and the words of every bucket are ordered by weight cell (x, y) (popc
-// of the high and of the low half of the fingerprint), and a segment is (tile
-// of tq patterns, dictionary bucket, run of cells): for the tile's cells
-// between its first and last pattern's, (x1, y1) .. (x2, y2) in cell order,
-// the tile's x lies in [x1, x2] and, when x1 = x2, its y in [y1, y2].  A word
-// with cell (x', y') can pass Eq. 1 for some pattern of the tile only if
-// dist(x', [x1, x2]) + dist(y', y-range) <= 2k (the halves' weight
-// differences add up to at most popc of the XOR).  So for every admissible x'
-// the tile tests one run of cells (x', y_lo .. y_hi), a run of slots in the
-// bucket; each run starts at the 8-slot boundary below its first word (the
-// words in between fail the bound too) so that tiles keep their aligned vector
-// loads, and runs that then touch or overlap are merged, so no pair is tested
-// twice.  "pairs" counts every eligible pair, tested or not; "tested" the
-// pairs the tiles test.
-struct PlanCounts {
-    int32_t nseg = 0;
-    uint64_t tiles = 0, pairs = 0, tested = 0;
-};
-
-constexpr int PLAN_MAX_BINS = 8192;  // 32 (k, metric) groups x 256 lengths
-
-__device__ __forceinline__ int slot_cell_of(const void *fp, int width, uint32_t s) {
-    return fp_cell(width == 16 ? (uint32_t)((const uint16_t *)fp)[s] : ((const uint32_t *)fp)[s], width);
-}
-
-template <bool WRITE>
-__device__ __forceinline__ void plan_emit(uint32_t q0, int qn, uint32_t nqt, uint32_t ds, uint32_t dn, int tw, int k,
-                                          int metric, Segment *seg, int max_segments, int64_t &si, uint64_t &tb,
-                                          PlanCounts &pc) {
-    const uint32_t ndt = (dn + (uint32_t)tw - 1u) / (uint32_t)tw;
-    pc.nseg++;
-    pc.tiles += (uint64_t)nqt * ndt;
-    pc.tested += (uint64_t)qn * dn;
-    if (WRITE) {
-        Segment sg;
-        sg.q_start = q0;
-        sg.q_count = (uint32_t)qn;
-        sg.d_start = ds;
-        sg.d_count = dn;
-        sg.n_qtiles = nqt;
-        sg.n_dtiles = ndt;
-        sg.tile_begin = tb;
-        sg.k = k;
-        sg.metric = metric;
-        if (si < max_segments) seg[si] = sg;
-        si++;
-        tb += (uint64_t)nqt * ndt;
-    }
-}
-
-__device__ __forceinline__ int64_t plan_units(int qc, bool band, int tq) {
-    return qc <= 0 ? 0 : (band ? (qc + tq - 1) / tq : 1);
-}
-
-// Unit u of bin c: the bin's patterns (no bands) or its u-th tile of tq
-// patterns; segments per dictionary bucket within the length window.
-template <bool WRITE>
-__device__ void plan_unit(int c, int64_t u, const int32_t *__restrict__ qb_start, const int32_t *__restrict__ qb_count,
-                          const int32_t *__restrict__ db_start, const int32_t *__restrict__ db_count,
-                          const int32_t *__restrict__ group_k, const int32_t *__restrict__ group_metric, int tq,
-                          int tw, const void *q_fp, int width, const int32_t *__restrict__ d_wstart, bool band,
-                          Segment *seg, int max_segments, int64_t &si, uint64_t &tb, PlanCounts &pc) {
-    const int qc = qb_count[c];
-    const int g = c >> 8, n = c & 255, k = group_k[g], metric = group_metric[g];
-    const int L0 = metric == FP_HAM ? n : (n - k < 0 ? 0 : n - k);
-    const int L1 = metric == FP_HAM ? n : (n + k > MAX_LEN ? MAX_LEN : n + k);
-    const uint32_t q0 = (uint32_t)qb_start[c] + (band ? (uint32_t)(u * tq) : 0u);
-    const int qn = band ? min(tq, qc - (int)(u * tq)) : qc;
-    const uint32_t nqt = band ? 1u : (uint32_t)((qc + tq - 1) / tq);
-    if (!band) {
-        for (int L = L0; L <= L1; L++) {
-            const int dc = db_count[L];
-            if (dc <= 0) continue;
-            pc.pairs += (uint64_t)qn * (uint64_t)dc;
-            plan_emit<WRITE>(q0, qn, nqt, (uint32_t)db_start[L], (uint32_t)dc, tw, k, metric, seg, max_segments, si, tb,
-                             pc);
-        }
-        return;
-    }
-    const int R = cell_radix(width), H = R - 1, NC = R * R, r2k = 2 * k;
-    const int cf = slot_cell_of(q_fp, width, q0), cl = slot_cell_of(q_fp, width, q0 + (uint32_t)qn - 1u);
-    const int x1 = cf / R, x2 = cl / R;
-    const int ya = x1 == x2 ? cf % R : 0, yb = x1 == x2 ? cl % R : H;  // the tile's y range
-    for (int L = L0; L <= L1; L++) {
-        const int dc = db_count[L];
-        if (dc <= 0) continue;
-        pc.pairs += (uint64_t)qn * (uint64_t)dc;
-        const int32_t *tab = d_wstart + (size_t)L * (NC + 1);
-        uint32_t ps = 0, pe = 0;  // pending run of slots [ps, pe)
-        bool pending = false;
-        for (int x = max(0, x1 - r2k); x <= min(H, x2 + r2k); x++) {
-            const int r = r2k - max(0, max(x1 - x, x - x2));
-            const int ylo = max(0, ya - r), yhi = min(H, yb + r);
-            const int32_t first = tab[x * R + ylo], end = tab[x * R + yhi + 1];
-            if (end <= first) continue;
-            const uint32_t s8 = (uint32_t)first & ~(uint32_t)(SLOT_ALIGN - 1);
-            if (pending && s8 <= pe) {
-                pe = max(pe, (uint32_t)end);
-            } else {
-                if (pending) plan_emit<WRITE>(q0, qn, 1u, ps, pe - ps, tw, k, metric, seg, max_segments, si, tb, pc);
-                ps = s8;
-                pe = (uint32_t)end;
-                pending = true;
-            }
-        }
-        if (pending) plan_emit<WRITE>(q0, qn, 1u, ps, pe - ps, tw, k, metric, seg, max_segments, si, tb, pc);
-    }
-}
-
-// One block of 1024 threads.  The units (bins, or tiles of bins with weight
-// bands) are numbered bin by bin; thread t plans units [t U / 1024,
-// (t + 1) U / 1024): a counting pass, a block scan of the segment and tile
-// counts, and a writing pass.
-__global__ void __launch_bounds__(1024) k_plan_segments(
-    const int32_t *__restrict__ qb_start, const int32_t *__restrict__ qb_count, int q_nbins,
-    const int32_t *__restrict__ db_start, const int32_t *__restrict__ db_count,
-    const int32_t *__restrict__ group_k, const int32_t *__restrict__ group_metric, int tq, int tw, const void *q_fp,
-    int width, const int32_t *__restrict__ d_wstart, Segment *__restrict__ seg, int max_segments,
-    uint64_t *__restrict__ scal) {
-    __shared__ int32_t s_unit0[PLAN_MAX_BINS + 1];  // first unit of every bin
-    __shared__ int32_t s_n[1024];
-    __shared__ uint64_t s_t[1024];
-    __shared__ unsigned long long s_pairs, s_tested;
-    const int t = threadIdx.x;
-    // a banded plan that does not fit falls back to whole buckets (which fit
-    // whenever max_segments >= bins x (2k + 1))
-    bool band = q_fp != nullptr && d_wstart != nullptr;
-    const int nbins = min(q_nbins, PLAN_MAX_BINS);
-    bool too_many = false;
-    int64_t u0 = 0, u1 = 0;
-    int c0 = 0;
-    PlanCounts pc;
-    for (;;) {
-        if (t == 0) {
-            s_pairs = 0;
-            s_tested = 0;
-        }
-        // units per bin and their prefix
-        {
-            const int per = (nbins + 1023) / 1024;
-            const int lo = min(nbins, t * per), hi = min(nbins, lo + per);
-            int64_t a = 0;
-            for (int c = lo; c < hi; c++) a += plan_units(qb_count[c], band, tq);
-            s_t[t] = (uint64_t)a;
-            __syncthreads();
-            for (int o = 1; o < 1024; o <<= 1) {
-                const uint64_t v = t >= o ? s_t[t - o] : 0;
-                __syncthreads();
-                s_t[t] += v;
-                __syncthreads();
-            }
-            int64_t r = (int64_t)s_t[t] - a;
-            for (int c = lo; c < hi; c++) {
-                s_unit0[c] = (int32_t)(r < 0x7FFFFFFF ? r : 0x7FFFFFFF);
-                r += plan_units(qb_count[c], band, tq);
-            }
-            if (t == 1023) s_unit0[nbins] = (int32_t)(s_t[1023] < 0x7FFFFFFFull ? s_t[1023] : 0x7FFFFFFFull);
-            __syncthreads();
-        }
-        too_many = s_t[1023] >= 0x7FFFFFFFull;  // units beyond int32: refuse the plan
-        const int64_t U = too_many ? 0 : s_unit0[nbins];
-        u0 = U * t / 1024;
-        u1 = U * (t + 1) / 1024;
-        {  // bin of unit u0: last bin whose first unit is <= u0
-            int lo = 0, hi = nbins - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (s_unit0[mid] <= u0) lo = mid;
-                else hi = mid - 1;
-            }
-            c0 = lo;
-        }
-        pc = PlanCounts{};
-        int64_t si = 0;
-        uint64_t tb = 0;
-        for (int64_t u = u0, c = c0; u < u1; u++) {
-            while (s_unit0[c + 1] <= u) c++;
-            plan_unit<false>((int)c, u - s_unit0[c], qb_start, qb_count, db_start, db_count, group_k, group_metric,
-                             tq, tw, q_fp, width, d_wstart, band, seg, max_segments, si, tb, pc);
-        }
-        s_n[t] = pc.nseg;
-        s_t[t] = pc.tiles;
-        atomicAdd(&s_pairs, (unsigned long long)pc.pairs);
-        atomicAdd(&s_tested, (unsigned long long)pc.tested);
-        __syncthreads();
-        for (int o = 1; o < 1024; o <<= 1) {
-            const int32_t a = t >= o ? s_n[t - o] : 0;
-            const uint64_t b = t >= o ? s_t[t - o] : 0;
-            __syncthreads();
-            s_n[t] += a;
-            s_t[t] += b;
-            __syncthreads();
-        }
-        if (!(band && s_n[1023] > max_segments)) break;
-        band = false;
-        __syncthreads();  // everyone has read s_n[1023] before it is reused
-    }
-    int64_t si;
-    uint64_t tb;
-    si = (int64_t)s_n[t] - pc.nseg;
-    tb = s_t[t] - pc.tiles;
-    PlanCounts again;
-    for (int64_t u = u0, c = c0; u < u1; u++) {
-        while (s_unit0[c + 1] <= u) c++;
-        plan_unit<true>((int)c, u - s_unit0[c], qb_start, qb_count, db_start, db_count, group_k, group_metric, tq,
-                        tw, q_fp, width, d_wstart, band, seg, max_segments, si, tb, again);
-    }
-    if (t == 1023) {
-        const int64_t ns = s_n[1023];
-        const bool over = ns > max_segments || q_nbins > PLAN_MAX_BINS || too_many;
-        scal[0] = (uint64_t)(ns < max_segments ? ns : max_segments);
-        scal[1] = over ? 0 : s_t[1023];  // refuse to run an incomplete plan
-        scal[2] = s_pairs;
-        scal[3] = 0;
-        scal[4] = 0;
-        scal[5] = 0;
-        scal[6] = over ? 1 : 0;
-        scal[7] = s_tested;
-    }
-}
-
-int plan_segments(const Bucketed &q, const Bucketed &d, const int32_t *d_group_k,
-                  const int32_t *d_group_metric, int tq, int tw, QueryPlan *plan, cudaStream_t st,
-                  const int32_t *d_wstart, int width) {
-    k_plan_segments<<<1, 1024, 0, st>>>(q.b_start, q.b_count, q.nbins, d.b_start, d.b_count, d_group_k,
-                                        d_group_metric, tq, tw, d_wstart ? q.fp : nullptr, width, d_wstart, plan->seg,
-                                        plan->max_segments, plan->scal);
-    FP_LAUNCHED("k_plan_segments");
-    return FP_OK;
-}
-
-// ---------------------------------------------------------------------------
 // distance functors
 // ---------------------------------------------------------------------------
 struct PosMasks {

@@ -48,7 +48,9 @@ __global__ void __launch_bounds__(RB_THREADS) k_radix_hist(const uint64_t *__res
 // consecutive values [8t, 8t + 8) of the tile, the per-thread sums are scanned
 // across the block (warp shuffles, then one shared step over the 32 warps),
 // and the tile is written back coalesced.  Shared indices are padded by one
-// word per 32 so that both access patterns are free of bank conflicts.
+// word per 32 so that both access patterns are free of bank conflicts.  The
+// next tile's loads are issued before the current tile is scanned, so their
+// latency overlaps the scan.
 constexpr int SCAN_R = 8, SCAN_TILE = 1024 * SCAN_R;
 
 __device__ __forceinline__ int scan_pad(int j) { return j + (j >> 5); }
@@ -59,11 +61,19 @@ __global__ void __launch_bounds__(1024) k_scan_u32(uint32_t *__restrict__ a, int
     __shared__ uint32_t s_carry;
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     if (t == 0) s_carry = 0;
+    uint32_t pre[SCAN_R];  // the tile about to be scanned, in coalesced order
+#pragma unroll
+    for (int r = 0; r < SCAN_R; r++) {
+        const int64_t i = r * 1024 + t;
+        pre[r] = i < n ? a[i] : 0u;
+    }
     for (int64_t base = 0; base < n; base += SCAN_TILE) {
 #pragma unroll
-        for (int r = 0; r < SCAN_R; r++) {
-            const int64_t i = base + r * 1024 + t;
-            s[scan_pad(r * 1024 + t)] = i < n ? a[i] : 0u;
+        for (int r = 0; r < SCAN_R; r++) s[scan_pad(r * 1024 + t)] = pre[r];
+#pragma unroll
+        for (int r = 0; r < SCAN_R; r++) {  // prefetch the next tile
+            const int64_t i = base + SCAN_TILE + r * 1024 + t;
+            pre[r] = i < n ? a[i] : 0u;
         }
         __syncthreads();
         uint32_t v[SCAN_R], sum = 0;
@@ -121,10 +131,12 @@ __global__ void __launch_bounds__(RB_THREADS) k_radix_scatter(const uint64_t *__
     uint64_t n = d_n ? min(*d_n, n_host) : n_host, lo, hi;
     block_range(n, nb, b, &lo, &hi);
     const unsigned lt = (1u << lane) - 1u;
+    uint64_t next = lo + t < hi ? in[lo + t] : 0;  // keys are loaded one chunk ahead
     for (uint64_t base = lo; base < hi; base += RB_THREADS) {
         uint64_t i = base + t;
         bool valid = i < hi;
-        uint64_t key = valid ? in[i] : 0;
+        const uint64_t key = next;
+        if (i + RB_THREADS < hi) next = in[i + RB_THREADS];
         uint32_t d = valid ? ((uint32_t)(key >> shift) & mask) : 256u;
 #pragma unroll
         for (int x = 0; x < RB_WARPS; x++) s_w[x][t] = 0;
