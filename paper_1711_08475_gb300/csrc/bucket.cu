@@ -486,23 +486,33 @@ __global__ void __launch_bounds__(256) k_weight_keys(Bucketed B, int width, cons
 }
 
 // Moves the slots into cell order: sorted key p of bin c goes to slot
-// b_start[c] + (p - U[c]); the old arrays are read from copies.
+// b_start[c] + (p - U[c]); the old arrays are read from copies.  The string
+// rows move with their slots, so that a bin's rows stay contiguous in slot
+// order (row of slot s = row of the bin's first slot + (s - first) x rows per
+// string), which the verifier relies on.
 __global__ void __launch_bounds__(256) k_weight_permute(const uint64_t *__restrict__ keys, int64_t n, Bucketed B,
                                                         int width, const int64_t *__restrict__ U,
                                                         const uint8_t *__restrict__ old_fp,
                                                         const int32_t *__restrict__ old_idx,
                                                         const uint8_t *__restrict__ old_len,
-                                                        const uint32_t *__restrict__ old_row16) {
+                                                        const uint32_t *__restrict__ old_row16,
+                                                        const uint8_t *__restrict__ old_str) {
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t key = keys[p];
         const int c = (int)(key >> (32 + CELL_BITS));
         const int64_t from = (int64_t)(key & 0xffffffffu);
-        const int64_t to = B.b_start[c] + (p - U[c]);
+        const int64_t first = B.b_start[c], to = first + (p - U[c]);
         if (width == 16) ((uint16_t *)B.fp)[to] = ((const uint16_t *)old_fp)[from];
         else ((uint32_t *)B.fp)[to] = ((const uint32_t *)old_fp)[from];
         B.idx[to] = old_idx[from];
-        B.len[to] = old_len[from];
-        B.row16[to] = old_row16[from];
+        const int L = old_len[from];
+        B.len[to] = (uint8_t)L;
+        const uint32_t rp = (uint32_t)((L + 15) >> 4);
+        const uint32_t row = old_row16[first] + (uint32_t)(to - first) * rp;  // the bin's rows start at its first slot's
+        B.row16[to] = row;
+        const uint4 *src = (const uint4 *)(old_str + (uint64_t)old_row16[from] * 16);
+        uint4 *dst = (uint4 *)(B.str + (uint64_t)row * 16);
+        for (uint32_t r = 0; r < rp; r++) dst[r] = src[r];
     }
 }
 
@@ -539,7 +549,8 @@ int weight_order(Bucketed *B, const FpParams &P, int32_t *d_wstart, cudaStream_t
     uint8_t *old = nullptr;
     int rc = FP_OK;
     const size_t o_idx = ((size_t)ns * fpw + 255) & ~(size_t)255, o_len = o_idx + (((size_t)ns * 4 + 255) & ~(size_t)255),
-                 o_row = o_len + (((size_t)ns + 255) & ~(size_t)255), total = o_row + (size_t)ns * 4;
+                 o_row = o_len + (((size_t)ns + 255) & ~(size_t)255),
+                 o_str = o_row + (((size_t)ns * 4 + 255) & ~(size_t)255), total = o_str + (size_t)B->str_bytes;
     cudaError_t e;
     if ((e = cudaMallocAsync((void **)&U, sizeof(int64_t) * (size_t)nbins, st)) != cudaSuccess ||
         (e = cudaMallocAsync((void **)&keys, sizeof(uint64_t) * (size_t)n, st)) != cudaSuccess ||
@@ -550,6 +561,8 @@ int weight_order(Bucketed *B, const FpParams &P, int32_t *d_wstart, cudaStream_t
                (e = cudaMemcpyAsync(old + o_idx, B->idx, (size_t)ns * 4, cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
                (e = cudaMemcpyAsync(old + o_len, B->len, (size_t)ns, cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
                (e = cudaMemcpyAsync(old + o_row, B->row16, (size_t)ns * 4, cudaMemcpyDeviceToDevice, st)) !=
+                   cudaSuccess ||
+               (e = cudaMemcpyAsync(old + o_str, B->str, (size_t)B->str_bytes, cudaMemcpyDeviceToDevice, st)) !=
                    cudaSuccess) {
         rc = cuda_fail(e, "weight_order: copies");
     } else {
@@ -563,7 +576,7 @@ int weight_order(Bucketed *B, const FpParams &P, int32_t *d_wstart, cudaStream_t
         if (rc == FP_OK) {
             k_weight_permute<<<grid_for(n, 256, 8192), 256, 0, st>>>(sorted, n, *B, P.width, U, old,
                                                                       (const int32_t *)(old + o_idx), old + o_len,
-                                                                      (const uint32_t *)(old + o_row));
+                                                                      (const uint32_t *)(old + o_row), old + o_str);
             rc = launched("k_weight_permute");
         }
         if (rc == FP_OK && d_wstart) {

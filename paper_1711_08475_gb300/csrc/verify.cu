@@ -44,6 +44,13 @@ struct VerifyArgs {
     const uint32_t *d_row16;
     const uint8_t *d_str;
     const int32_t *d_idx;
+    // rows by slot: both sets have one group of 256 length bins whose rows are
+    // contiguous in slot order (bucketing writes them so, the weight order
+    // moves them with their slots), so the row of a slot follows from its
+    // length and the bin's first slot and row, kept in shared memory: one
+    // gather fewer per string
+    const int32_t *q_bstart, *q_bcount, *d_bstart, *d_bcount;
+    int rows_by_slot;
     int idx_bits;
     uint64_t *matches;
     uint64_t *n_matches;
@@ -78,16 +85,30 @@ __device__ __forceinline__ void flush_matches(const VerifyArgs &A, uint64_t *sta
     __syncwarp();
 }
 
+// Resident blocks per SM the register budget is set for.
+#ifndef VERIFY_MIN_BLOCKS
+#define VERIFY_MIN_BLOCKS 4  // measured against 1 and 3 (Hamming keeps 64 registers instead of 80)
+#endif
+
 template <int METRIC, int K>
-__global__ void __launch_bounds__(256) k_verify(VerifyArgs A, int k) {
+__global__ void __launch_bounds__(256, VERIFY_MIN_BLOCKS) k_verify(VerifyArgs A, int k) {
     constexpr int U = VERIFY_U;
     __shared__ uint64_t s_stage[8][VSTAGE];
     __shared__ uint32_t s_cnt[8];
+    __shared__ uint32_t s_first[2][256], s_row0[2][256];  // per length bin: first slot, its row
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint64_t *stage = s_stage[warp];
     uint32_t *cnt = &s_cnt[warp];
     if (lane == 0) *cnt = 0;
-    __syncwarp();
+    if (A.rows_by_slot) {
+        const int t = threadIdx.x;  // blockDim.x == 256
+        const int32_t qf = A.q_bstart[t], df = A.d_bstart[t];
+        s_first[0][t] = (uint32_t)qf;
+        s_row0[0][t] = A.q_bcount[t] > 0 ? A.q_row16[qf] : 0u;
+        s_first[1][t] = (uint32_t)df;
+        s_row0[1][t] = A.d_bcount[t] > 0 ? A.d_row16[df] : 0u;
+    }
+    __syncthreads();
     const uint64_t n0 = *A.n_surv;
     const uint64_t n = n0 < A.surv_cap ? n0 : A.surv_cap;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x * U;
@@ -109,8 +130,13 @@ __global__ void __launch_bounds__(256) k_verify(VerifyArgs A, int k) {
                 const uint32_t qs = (uint32_t)(s[u] >> 32), ds = (uint32_t)s[u];
                 m[u] = A.q_len[qs];
                 L[u] = A.d_len[ds];
-                qr[u] = A.q_row16[qs];
-                dr[u] = A.d_row16[ds];
+                if (A.rows_by_slot) {
+                    qr[u] = s_row0[0][m[u]] + (qs - s_first[0][m[u]]) * (uint32_t)((m[u] + 15) >> 4);
+                    dr[u] = s_row0[1][L[u]] + (ds - s_first[1][L[u]]) * (uint32_t)((L[u] + 15) >> 4);
+                } else {
+                    qr[u] = A.q_row16[qs];
+                    dr[u] = A.d_row16[ds];
+                }
             } else {
                 m[u] = -1;
                 L[u] = -2;
@@ -213,6 +239,11 @@ int launch_verify(const Bucketed &q, const Bucketed &d, const uint64_t *surv, co
     A.d_row16 = d.row16;
     A.d_str = d.str;
     A.d_idx = d.idx;
+    A.q_bstart = q.b_start;
+    A.q_bcount = q.b_count;
+    A.d_bstart = d.b_start;
+    A.d_bcount = d.b_count;
+    A.rows_by_slot = q.nbins == 256 && d.nbins == 256;
     A.idx_bits = idx_bits;
     A.matches = matches;
     A.n_matches = d_n_matches;
