@@ -496,12 +496,13 @@ int fp_query_ex(fp_index *ix, const uint8_t *chars, const int64_t *offsets, int6
     CK(cudaMemsetAsync(R.d_err, 0, sizeof(int32_t), st));
     TRY(bucketize(S.chars, S.off, n_queries, S.total, nullptr, 1, ix->d_map, ix->P, true, st, &R.Q, R.d_err, band));
     // weight bands: patterns in cell order; per tile of tq patterns and
-    // dictionary bucket at most one run of cells per high-half weight (the
-    // plain scan tests every pair)
+    // dictionary bucket a few runs of cells (at most one per admissible
+    // (x, y)); a plan that needs more than 32 per (tile, bucket) on average
+    // falls back to whole buckets on the device (the plain scan tests every
+    // pair)
     if (band) {
         R.plan.max_segments = (int)std::min<int64_t>(
-            0x7FFFFFFF, ((n_queries + tq - 1) / tq + 256) * (metric == FP_HAM ? 1 : 2 * k + 1) *
-                            cell_radix(ix->P.width));
+            0x7FFFFFFF, ((n_queries + tq - 1) / tq + 256) * (metric == FP_HAM ? 1 : 2 * k + 1) * 32);
     } else {
         R.plan.max_segments = 256 * (2 * k + 1);
     }

@@ -208,7 +208,8 @@ __global__ void k_bin_keys(const int64_t *__restrict__ off, int64_t n, const int
 }
 
 
-constexpr int CELL_BITS = 9;  // cell_count(32) = 289 < 512
+constexpr int CELL_BITS = 11;  // cell_count(32) = 12 x 12 x 11 = 1584 < 2048
+static_assert(cell_count(32) < (1 << CELL_BITS) && cell_count(16) < (1 << CELL_BITS), "cell keys");
 
 // k_bin_keys with the weight cell of each string's fingerprint between the bin
 // and the index, so that the sort leaves every bin in cell order.

@@ -94,15 +94,22 @@ int bucketize(const uint8_t *d_chars, const int64_t *d_off, int64_t n, int64_t t
 void free_bucketed(Bucketed *b, cudaStream_t st);
 // Rebuilds fingerprints of an existing bucketed set from its rows.
 int refingerprint(Bucketed *b, const int8_t *d_map, const FpParams &fp, cudaStream_t st);
-// Weight cells.  A fingerprint f of width W has the cell (x, y) = (popc of
-// its high W/2 bits, popc of its low W/2 bits), numbered x * (W/2 + 1) + y.
-// For two fingerprints |x - x'| + |y - y'| <= popc(f ^ f'), so a pair whose
-// cells lie more than 2k apart (L1) fails Eq. 1.
-__host__ __device__ constexpr int cell_radix(int width) { return width / 2 + 1; }
-__host__ __device__ constexpr int cell_count(int width) { return cell_radix(width) * cell_radix(width); }
+// Weight cells.  The W bits of a fingerprint are split into three parts of
+// ceil / floor(W/3) bits (W = 32: bits 21..31, 10..20, 0..9; W = 16: 10..15,
+// 5..9, 0..4); its cell is (x, y, z) = the population counts of the parts,
+// numbered (x * R1 + y) * R2 + z with R_i = bits of part i + 1.  Every bit
+// that differs between two fingerprints changes one part's count by one, so
+// |x - x'| + |y - y'| + |z - z'| <= popc(f ^ f'): a pair whose cells lie more
+// than 2k apart (L1) fails Eq. 1.
+__host__ __device__ constexpr int cell_part_bits(int width, int i) { return width / 3 + (i < width % 3 ? 1 : 0); }
+__host__ __device__ constexpr int cell_part_radix(int width, int i) { return cell_part_bits(width, i) + 1; }
+__host__ __device__ constexpr int cell_count(int width) {
+    return cell_part_radix(width, 0) * cell_part_radix(width, 1) * cell_part_radix(width, 2);
+}
 __device__ __forceinline__ int fp_cell(uint32_t f, int width) {
-    const int h = width / 2;
-    return __popc(f >> h) * (h + 1) + __popc(f & ((1u << h) - 1u));
+    const int b1 = cell_part_bits(width, 1), b2 = cell_part_bits(width, 2);
+    const int x = __popc(f >> (b1 + b2)), y = __popc((f >> b2) & ((1u << b1) - 1u)), z = __popc(f & ((1u << b2) - 1u));
+    return (x * (b1 + 1) + y) * (b2 + 1) + z;
 }
 // Orders the real slots of every bin by weight cell (stable), for occurrence,
 // occurrence-halved and count fingerprints (a no-op for position

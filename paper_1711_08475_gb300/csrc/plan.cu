@@ -58,10 +58,10 @@ size_t pipe_layout(const PipeShape &s, uint8_t *base, Pipe *p) {
     const int64_t strb = s.chars + 15 * n + STR_SLACK;
     const int64_t cap = std::max<int64_t>(s.match_cap, 1);
     const int64_t rh = 256 * (int64_t)std::max(radix_blocks(cap), radix_blocks(n));
-    // segments: whole buckets need bins x 31 at most; weight bands about 18 per
-    // tile of 64 patterns (three lengths, a few runs of cells each) -- a plan
-    // that needs more falls back to whole buckets on the device
-    const int64_t seg_cap = std::min<int64_t>(0x7FFFFFFF, std::max<int64_t>(nbins * 31, (n / 64 + nbins) * 18));
+    // segments: whole buckets need bins x 31 at most; weight bands about 40 per
+    // tile of 64 patterns (three lengths, several runs of cells each) -- a
+    // plan that needs more falls back to whole buckets on the device
+    const int64_t seg_cap = std::min<int64_t>(0x7FFFFFFF, std::max<int64_t>(nbins * 31, (n / 64 + nbins) * 40));
     size_t off = 0;
     const size_t o_chars = carve(off, (size_t)s.chars + 16), o_off = carve(off, 8 * (size_t)(n + 1)),
                  o_bs = carve(off, 8 * (size_t)(s.batches + 1)), o_bg = carve(off, 4 * (size_t)s.batches),

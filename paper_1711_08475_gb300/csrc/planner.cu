@@ -17,20 +17,21 @@ namespace fpk {
 // ---------------------------------------------------------------------------
 // Without weight bands a segment is (query bin, dictionary bucket) with
 // ceil(q/tq) x ceil(d/tw) tiles.  With weight bands the patterns of every
-// bin and the words of every bucket are ordered by weight cell (x, y) (popc
-// of the high and of the low half of the fingerprint), and a segment is (tile
-// of tq patterns, dictionary bucket, run of cells): for the tile's cells
-// between its first and last pattern's, (x1, y1) .. (x2, y2) in cell order,
-// the tile's x lies in [x1, x2] and, when x1 = x2, its y in [y1, y2].  A word
-// with cell (x', y') can pass Eq. 1 for some pattern of the tile only if
-// dist(x', [x1, x2]) + dist(y', y-range) <= 2k (the halves' weight
-// differences add up to at most popc of the XOR).  So for every admissible x'
-// the tile tests one run of cells (x', y_lo .. y_hi), a run of slots in the
-// bucket; each run starts at the 8-slot boundary below its first word (the
-// words in between fail the bound too) so that tiles keep their aligned vector
-// loads, and runs that then touch or overlap are merged, so no pair is tested
-// twice.  "pairs" counts every eligible pair, tested or not; "tested" the
-// pairs the tiles test.
+// bin and the words of every bucket are ordered by weight cell (x, y, z)
+// (fp_cell: the population counts of the fingerprint's three parts), and a
+// segment is (tile of tq patterns, dictionary bucket, run of cells).  From
+// the cells of the tile's first and last pattern, (x1, y1, z1) and
+// (x2, y2, z2) in cell (lexicographic) order, the tile's box is x in
+// [x1, x2], y in [y1, y2] when x1 = x2 (else all), z in [z1, z2] when also
+// y1 = y2 (else all).  A word with cell (x', y', z') can pass Eq. 1 for some
+// pattern of the tile only if its L1 distance to the box is at most 2k (the
+// parts' weight differences add up to at most popc of the XOR).  So for every
+// admissible (x', y') the tile tests one run of cells (x', y', z_lo .. z_hi),
+// a run of slots in the bucket; each run starts at the 8-slot boundary below
+// its first word (the words in between fail the bound too) so that tiles keep
+// their aligned vector loads, and runs that then touch or overlap are merged,
+// so no pair is tested twice.  "pairs" counts every eligible pair, tested or
+// not; "tested" the pairs the tiles test.
 struct PlanCounts {
     int32_t nseg = 0;
     uint64_t tiles = 0, pairs = 0, tested = 0;
@@ -97,11 +98,16 @@ __device__ void plan_unit(int c, int64_t u, const int32_t *__restrict__ qb_start
         }
         return;
     }
-    const int R = cell_radix(width), H = R - 1, NC = R * R, r2k = 2 * k;
+    const int R1 = cell_part_radix(width, 1), R2 = cell_part_radix(width, 2), NC = cell_count(width);
+    const int H0 = cell_part_bits(width, 0), H1 = R1 - 1, H2 = R2 - 1, r2k = 2 * k;
     const int cf = slot_cell_of(q_fp, width, q0), cl = slot_cell_of(q_fp, width, q0 + (uint32_t)qn - 1u);
-    const int x1 = cf / R, x2 = cl / R;
-    const int ya = x1 == x2 ? cf % R : 0, yb = x1 == x2 ? cl % R : H;  // the tile's y range
-    const int xlo = max(0, x1 - r2k), xhi = min(H, x2 + r2k);
+    // the tile's box from its first and last pattern (cell order is
+    // lexicographic in (x, y, z))
+    const int xa = cf / (R1 * R2), xb = cl / (R1 * R2);
+    const int y1 = cf / R2 % R1, y2 = cl / R2 % R1, z1 = cf % R2, z2 = cl % R2;
+    const int ya = xa == xb ? y1 : 0, yb = xa == xb ? y2 : H1;
+    const int za = xa == xb && y1 == y2 ? z1 : 0, zb = xa == xb && y1 == y2 ? z2 : H2;
+    const int xlo = max(0, xa - r2k), xhi = min(H0, xb + r2k);
     for (int L = L0; L <= L1; L++) {
         const int dc = db_count[L];
         if (dc <= 0) continue;
@@ -109,35 +115,40 @@ __device__ void plan_unit(int c, int64_t u, const int32_t *__restrict__ qb_start
         const int32_t *tab = d_wstart + (size_t)L * (NC + 1);
         uint32_t ps = 0, pe = 0;  // pending run of slots [ps, pe)
         bool pending = false;
-        // the runs of PLAN_CHUNK consecutive x' at a time: their table loads
-        // are all in flight at once, then merged in order
-        for (int xb = xlo; xb <= xhi; xb += PLAN_CHUNK) {
-            int32_t fs[PLAN_CHUNK], es[PLAN_CHUNK];
+        for (int x = xlo; x <= xhi; x++) {
+            const int r1 = r2k - max(0, max(xa - x, x - xb));
+            const int ylo = max(0, ya - r1), yhi = min(H1, yb + r1);
+            // the runs of PLAN_CHUNK consecutive y' at a time: their table
+            // loads are all in flight at once, then merged in order
+            for (int yc = ylo; yc <= yhi; yc += PLAN_CHUNK) {
+                int32_t fs[PLAN_CHUNK], es[PLAN_CHUNK];
 #pragma unroll
-            for (int j = 0; j < PLAN_CHUNK; j++) {
-                const int x = xb + j;
-                fs[j] = 0;
-                es[j] = 0;
-                if (x <= xhi) {
-                    const int r = r2k - max(0, max(x1 - x, x - x2));
-                    const int ylo = max(0, ya - r), yhi = min(H, yb + r);
-                    fs[j] = tab[x * R + ylo];
-                    es[j] = tab[x * R + yhi + 1];
+                for (int j = 0; j < PLAN_CHUNK; j++) {
+                    const int y = yc + j;
+                    fs[j] = 0;
+                    es[j] = 0;
+                    if (y <= yhi) {
+                        const int r2 = r1 - max(0, max(ya - y, y - yb));
+                        const int zlo = max(0, za - r2), zhi = min(H2, zb + r2);
+                        const int cxy = (x * R1 + y) * R2;
+                        fs[j] = tab[cxy + zlo];
+                        es[j] = tab[cxy + zhi + 1];
+                    }
                 }
-            }
 #pragma unroll
-            for (int j = 0; j < PLAN_CHUNK; j++) {
-                const int32_t first = fs[j], end = es[j];
-                if (end <= first) continue;
-                const uint32_t s8 = (uint32_t)first & ~(uint32_t)(SLOT_ALIGN - 1);
-                if (pending && s8 <= pe) {
-                    pe = max(pe, (uint32_t)end);
-                } else {
-                    if (pending)
-                        plan_emit<WRITE>(q0, qn, 1u, ps, pe - ps, tw, k, metric, seg, max_segments, si, tb, pc);
-                    ps = s8;
-                    pe = (uint32_t)end;
-                    pending = true;
+                for (int j = 0; j < PLAN_CHUNK; j++) {
+                    const int32_t first = fs[j], end = es[j];
+                    if (end <= first) continue;
+                    const uint32_t s8 = (uint32_t)first & ~(uint32_t)(SLOT_ALIGN - 1);
+                    if (pending && s8 <= pe) {
+                        pe = max(pe, (uint32_t)end);
+                    } else {
+                        if (pending)
+                            plan_emit<WRITE>(q0, qn, 1u, ps, pe - ps, tw, k, metric, seg, max_segments, si, tb, pc);
+                        ps = s8;
+                        pe = (uint32_t)end;
+                        pending = true;
+                    }
                 }
             }
         }

@@ -1,12 +1,13 @@
 """Weight bands (needs a GPU).
 
-The buckets are ordered by weight cell (popc of the fingerprint's high half,
-popc of its low half) and every query tile tests only the runs of cells whose
-L1 distance to the tile's cells is at most 2k: the halves' weight differences
-add up to at most popc(a ^ b), so the skipped pairs fail Eq. 1 (pinned on the
-CPU in test_oracle_pins.py).  Here: the match lists and the survivor count
-stay the oracle's, and the number of pairs the filter tested equals the count
-of a plain re-statement of the band rule on the oracle's fingerprints.
+The buckets are ordered by weight cell (the population counts of three parts
+of the fingerprint) and every query tile tests only the runs of cells whose L1
+distance to the tile's box of cells is at most 2k: the parts' weight
+differences add up to at most popc(a ^ b), so the skipped pairs fail Eq. 1
+(pinned on the CPU in test_oracle_pins.py).  Here: the match lists and the
+survivor count stay the oracle's, and the number of pairs the filter tested
+equals the count of a plain re-statement of the band rule on the oracle's
+fingerprints.
 """
 import numpy as np
 import pytest
@@ -34,52 +35,69 @@ def popc(x):
     return np.array([bin(int(v)).count("1") for v in x], dtype=np.int64)
 
 
+def part_bits(width):
+    """Bits of the three parts, most significant part first (W = 32: 11, 11, 10)."""
+    return [width // 3 + (1 if i < width % 3 else 0) for i in range(3)]
+
+
 def cells(f, width):
-    h = width // 2
+    b0, b1, b2 = part_bits(width)
     f = np.asarray(f, dtype=np.uint64)
-    return popc(f >> np.uint64(h)) * (h + 1) + popc(f & np.uint64((1 << h) - 1))
+    x = popc(f >> np.uint64(b1 + b2))
+    y = popc((f >> np.uint64(b2)) & np.uint64((1 << b1) - 1))
+    z = popc(f & np.uint64((1 << b2) - 1))
+    return (x * (b1 + 1) + y) * (b2 + 1) + z
 
 
 def expected_tested(d, q, k, metric, m, t, width, tq):
     """Pairs a banded plan tests.  Per length bin the patterns sorted by cell
-    are cut into tiles of tq; with (x1, y1), (x2, y2) the cells of a tile's
-    first and last pattern, its x range is [x1, x2] and its y range [y1, y2]
-    when x1 = x2, else everything.  In every dictionary bucket of an
-    admissible length and for every x' within 2k of the x range, the tile
-    tests the words of cells (x', y') with y' within the remaining distance of
-    the y range: one run of slots, started at the bucket's 8-slot boundary
-    below its first word; runs that then touch or overlap are merged."""
-    R = width // 2 + 1
-    H = R - 1
+    are cut into tiles of tq.  With (x1, y1, z1), (x2, y2, z2) the cells of a
+    tile's first and last pattern, its box is x in [x1, x2], y in [y1, y2] if
+    x1 = x2 (else everything), z in [z1, z2] if also y1 = y2 (else
+    everything).  In every dictionary bucket of an admissible length, for
+    every (x', y') whose L1 distance to the box's x and y ranges is at most
+    2k, the tile tests the words of cells (x', y', z') with z' within the
+    remaining distance of the z range: one run of slots, started at the
+    bucket's 8-slot boundary below its first word; runs that then touch or
+    overlap are merged."""
+    b0, b1, b2 = part_bits(width)
+    R1, R2 = b1 + 1, b2 + 1
     cq = cells(oracle.fingerprints(q, m, t, width), width)
     cd = cells(oracle.fingerprints(d, m, t, width), width)
     lq, ld = q.lengths(), d.lengths()
     by_len = {L: np.sort(cd[ld == L]) for L in np.unique(ld)}
+    dist = lambda v, lo, hi: max(lo - v, 0, v - hi)
     total = 0
     for n in np.unique(lq):
         cs = np.sort(cq[lq == n])
         lens = [n] if metric == "ham" else range(max(0, n - k), min(255, n + k) + 1)
         for s in range(0, len(cs), tq):
             tile = cs[s:s + tq]
-            x1, x2 = int(tile[0]) // R, int(tile[-1]) // R
-            ya, yb = (int(tile[0]) % R, int(tile[-1]) % R) if x1 == x2 else (0, H)
+            f, l = int(tile[0]), int(tile[-1])
+            xa, xb = f // (R1 * R2), l // (R1 * R2)
+            y1, y2, z1, z2 = f // R2 % R1, l // R2 % R1, f % R2, l % R2
+            ya, yb = (y1, y2) if xa == xb else (0, b1)
+            za, zb = (z1, z2) if xa == xb and y1 == y2 else (0, b2)
             for L in lens:
                 if L not in by_len:
                     continue
                 b = by_len[L]
                 runs = []
-                for x in range(max(0, x1 - 2 * k), min(H, x2 + 2 * k) + 1):
-                    r = 2 * k - max(0, x1 - x, x - x2)
-                    ylo, yhi = max(0, ya - r), min(H, yb + r)
-                    first = int(np.searchsorted(b, x * R + ylo, side="left"))
-                    end = int(np.searchsorted(b, x * R + yhi + 1, side="left"))
-                    if end <= first:
-                        continue
-                    s8 = first & ~7
-                    if runs and s8 <= runs[-1][1]:
-                        runs[-1][1] = max(runs[-1][1], end)
-                    else:
-                        runs.append([s8, end])
+                for x in range(max(0, xa - 2 * k), min(b0, xb + 2 * k) + 1):
+                    r1 = 2 * k - dist(x, xa, xb)
+                    for y in range(max(0, ya - r1), min(b1, yb + r1) + 1):
+                        r2 = r1 - dist(y, ya, yb)
+                        zlo, zhi = max(0, za - r2), min(b2, zb + r2)
+                        c = (x * R1 + y) * R2
+                        first = int(np.searchsorted(b, c + zlo, side="left"))
+                        end = int(np.searchsorted(b, c + zhi + 1, side="left"))
+                        if end <= first:
+                            continue
+                        s8 = first & ~7
+                        if runs and s8 <= runs[-1][1]:
+                            runs[-1][1] = max(runs[-1][1], end)
+                        else:
+                            runs.append([s8, end])
                 total += len(tile) * sum(e - a for a, e in runs)
     return total
 
@@ -158,7 +176,7 @@ def test_band_at_scale(fp, metric):
     d, q = w.dictionary, w.queries[metric]
     ix = fp.fp_build(d, fp_type="count", width=32)
     m = ix.symbol_map()
-    for tq in (256, 64):
+    for tq in (128, 64):
         r = fp.fp_query_ex(ix, q, k=1, metric=metric, tile_queries=tq)
         st = r.stats()
         rp0, idx0 = oracle.match(d, q, 1, metric)

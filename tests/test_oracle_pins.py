@@ -43,20 +43,28 @@ def test_filter_is_pure_speedup_uniform10k(orc):
 
 
 def test_weight_difference_bounds_fd(orc):
-    """popc(a ^ b) >= |popc(a) - popc(b)| on the oracle's own fingerprints, so a
-    pair whose weights differ by more than 2k fails Eq. 1; the GPU path skips
-    such pairs by weight-ordering its buckets."""
+    """popc(a ^ b) >= sum over the parts of |popc(a_part) - popc(b_part)|, for
+    one part (the whole word) and for the three parts of the weight cells
+    (W = 32: bits 21..31, 10..20, 0..9; W = 16: 10..15, 5..9, 0..4), on the
+    oracle's own fingerprints: a pair whose cells are more than 2k apart fails
+    Eq. 1, which is what lets the GPU path skip it."""
     w = datagen.english1m(3000, 400)
     for t, width in (("occ", 32), ("count", 32), ("occ", 16), ("occh", 16)):
         m, _, _ = orc.symbol_map(w.dictionary.chars, "common", oracle.layout(t, width)["sigma"])
         a = orc.fingerprints(w.dictionary, m, t, width).astype(np.uint64)
         b = orc.fingerprints(w.queries["ham"], m, t, width).astype(np.uint64)
-        pa = np.array([bin(int(x)).count("1") for x in a])
-        pb = np.array([bin(int(x)).count("1") for x in b])
         x = a[None, :] ^ b[:, None]
         fdx = np.zeros(x.shape, dtype=np.int64)
         for s in range(32):
             fdx += ((x >> np.uint64(s)) & np.uint64(1)).astype(np.int64)
-        dw = np.abs(pa[None, :] - pb[:, None])
-        assert (fdx >= dw).all()
-        assert (fdx == dw).any() and (fdx > dw).any()  # both cases occur
+        bits = [width // 3 + (1 if i < width % 3 else 0) for i in range(3)]
+        shifts = [bits[1] + bits[2], bits[2], 0]
+        for parts in ([(0, width)], list(zip(shifts, bits))):
+            dw = np.zeros(x.shape, dtype=np.int64)
+            for sh, nb in parts:
+                mask = np.uint64((1 << nb) - 1)
+                pa = np.array([bin(int(v)).count("1") for v in (a >> np.uint64(sh)) & mask])
+                pb = np.array([bin(int(v)).count("1") for v in (b >> np.uint64(sh)) & mask])
+                dw += np.abs(pa[None, :] - pb[:, None])
+            assert (fdx >= dw).all()
+            assert (fdx == dw).any() and (fdx > dw).any()  # both cases occur
