@@ -56,6 +56,13 @@ constexpr int FT_QUEUE = 256;  // queued (lane, tile query) hits per warp
 #ifndef FT_UNROLL
 #define FT_UNROLL 1  // groups of four queries unrolled in the loop over a partial batch
 #endif
+#ifndef FT_SPLIT_FULL
+// 0: one copy of the pattern loop for whole and short tiles; a short tile's
+// fingerprints past its end are tested like the others and masked in the
+// exact re-test (a hit there only costs a re-test).  1: a masked copy of the
+// loop for short tiles.
+#define FT_SPLIT_FULL 0
+#endif
 #define FT_STR(x) #x
 #define FT_UNROLL_PRAGMA(n) _Pragma(FT_STR(unroll n))
 
@@ -394,11 +401,13 @@ __device__ __forceinline__ void scan_tile(const FilterArgs &A, const uint32_t *s
         if (!FUSED && jn == 32u) {  // a whole batch: fully unrolled (the fused form is faster without)
 #pragma unroll
             for (uint32_t jj = 0; jj < 32u; jj += 4)
-                hits = four_queries<W, V, POS, FULL, K1MIX>(w, s_q4[(jb + jj) >> 2], A.M, invalid, T, hits);
+                hits = four_queries<W, V, POS, FULL || !FT_SPLIT_FULL, K1MIX>(w, s_q4[(jb + jj) >> 2], A.M, invalid, T,
+                                                                              hits);
         } else {
             FT_UNROLL_PRAGMA(FT_UNROLL)
             for (uint32_t jj = 0; jj < jn; jj += 4)
-                hits = four_queries<W, V, POS, FULL, K1MIX>(w, s_q4[(jb + jj) >> 2], A.M, invalid, T, hits);
+                hits = four_queries<W, V, POS, FULL || !FT_SPLIT_FULL, K1MIX>(w, s_q4[(jb + jj) >> 2], A.M, invalid, T,
+                                                                              hits);
         }
         hits &= ~((1u << (jn4 - jn)) - 1u);  // queries past nq in the last group of four
         const uint32_t c = __popc(hits);
@@ -542,13 +551,13 @@ __global__ void __launch_bounds__(FT_THREADS, (ft_min_blocks<W, V, POS, FUSED>()
         if (nvalid == 0u || qn == 0u) {
             // nothing for this warp in a short tile
         } else if (K1MIX && T != 2u) {  // a k = 1 variant given another k: exact general path
-            if (nw == (uint32_t)TW)
+            if (FT_SPLIT_FULL && nw == (uint32_t)TW)
                 scan_tile<W, V, POS, true, false, FUSED>(A, s_q + qa, qn, q0 + qa, w, invalid, T, wbase, stage, cnt, queue, qcnt, lane,
                                                            S.k, S.metric);
             else
                 scan_tile<W, V, POS, false, false, FUSED>(A, s_q + qa, qn, q0 + qa, w, invalid, T, wbase, stage, cnt, queue, qcnt, lane,
                                                            S.k, S.metric);
-        } else if (nw == (uint32_t)TW) {
+        } else if (FT_SPLIT_FULL && nw == (uint32_t)TW) {
             scan_tile<W, V, POS, true, K1MIX, FUSED>(A, s_q + qa, qn, q0 + qa, w, invalid, T, wbase, stage, cnt, queue, qcnt, lane,
                                                            S.k, S.metric);
         } else {
