@@ -38,7 +38,10 @@ struct PlanCounts {
 };
 
 constexpr int PLAN_MAX_BINS = 8192;  // 32 (k, metric) groups x 256 lengths
-constexpr int PLAN_CHUNK = 6;  // table loads a planner thread keeps in flight per length
+constexpr int PLAN_CHUNK = 6;
+#ifndef PLAN_MERGE_GAP
+#define PLAN_MERGE_GAP 0u  // runs closer than this many slots are merged (the gap's words are tested too)
+#endif  // table loads a planner thread keeps in flight per length
 
 __device__ __forceinline__ int slot_cell_of(const void *fp, int width, uint32_t s) {
     return fp_cell(width == 16 ? (uint32_t)((const uint16_t *)fp)[s] : ((const uint32_t *)fp)[s], width);
@@ -140,7 +143,7 @@ __device__ void plan_unit(int c, int64_t u, const int32_t *__restrict__ qb_start
                     const int32_t first = fs[j], end = es[j];
                     if (end <= first) continue;
                     const uint32_t s8 = (uint32_t)first & ~(uint32_t)(SLOT_ALIGN - 1);
-                    if (pending && s8 <= pe) {
+                    if (pending && s8 <= pe + PLAN_MERGE_GAP) {
                         pe = max(pe, (uint32_t)end);
                     } else {
                         if (pending)
