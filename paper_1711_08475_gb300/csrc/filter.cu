@@ -30,25 +30,29 @@
 
 namespace fpk {
 
-constexpr int FT_THREADS = 256;
+#ifndef FT_THREADS
+#define FT_THREADS 128  // threads per block of the tiled filter (measured against 256)
+#endif
 constexpr int FT_WARPS = FT_THREADS / 32;
 constexpr int FT_MAX_TQ = 256;
 constexpr int FT_STAGE = 256;  // staged survivors per warp
 constexpr int FT_QUEUE = 256;  // queued (lane, tile query) hits per warp
 
 // Tuning constants (compile-time; the defaults come from sweeps on GB300).
-// Resident blocks per SM the register budget is set for: the 32-bit,
-// 4-words-per-thread filter fits 32 registers without spilling (8 blocks, 64
-// warps); the other shapes keep 48; the fused form, which calls the verifier,
-// is fastest at 64 registers (4 blocks; a few spills, measured against 3 and 5).
+// Resident blocks per SM the register budget is set for (blocks of 128
+// threads): the 32-bit, 4-words-per-thread filter fits 32 registers (16
+// blocks, 64 warps); the other shapes keep 48 (10 blocks); the fused form,
+// which calls the verifier, is fastest at 64 registers (8 blocks; a few
+// spills).  Four-warp blocks beat eight-warp ones by 1-2 %: fewer warps wait
+// at a tile's barrier for the slowest one.
 #ifndef FT_MIN_BLOCKS
-#define FT_MIN_BLOCKS 5
+#define FT_MIN_BLOCKS 10
 #endif
 #ifndef FT_MAIN_MIN_BLOCKS
-#define FT_MAIN_MIN_BLOCKS 8
+#define FT_MAIN_MIN_BLOCKS 16
 #endif
 #ifndef FT_FUSED_MIN_BLOCKS
-#define FT_FUSED_MIN_BLOCKS 4
+#define FT_FUSED_MIN_BLOCKS 8
 #endif
 #ifndef FT_MIX_DIV
 #define FT_MIX_DIV 4  // k = 1 mix: V / FT_MIX_DIV of a thread's words use the ALU-only test
@@ -193,10 +197,10 @@ __device__ __forceinline__ int find_segment_warp(const Segment *seg, int nseg, u
 
 // Thread layout of a tile.  Fingerprints arrive in 128-bit vectors of G
 // fingerprints (G = 4 for 32-bit, 8 for 16-bit); vector r of thread t holds
-// the tile's fingerprints r*(256*G) + t*G + (0..G-1), so one warp-wide load
+// the tile's fingerprints r*(T*G) + t*G + (0..G-1) (T = FT_THREADS), so one warp-wide load
 // reads 512 contiguous bytes.  Fingerprint i of a thread (0 <= i < NF) is at
-// tile offset (i/G)*(256*G) + t*G + i%G; relative to the warp's first slot it
-// is (i/G)*(256*G) + lane*G + i%G.
+// tile offset (i/G)*(T*G) + t*G + i%G; relative to the warp's first slot it
+// is (i/G)*(T*G) + lane*G + i%G.
 template <int G>
 __device__ __forceinline__ uint32_t lane_offset(int i, int lane) {
     return (uint32_t)(i / G) * (uint32_t)(FT_THREADS * G) + (uint32_t)lane * G + (uint32_t)(i % G);
@@ -520,8 +524,8 @@ __global__ void __launch_bounds__(FT_THREADS, (ft_min_blocks<W, V, POS, FUSED>()
         }
         __syncthreads();
         // A short tile (the end of a run of weight cells) has fingerprints for
-        // nch < 8 warps' columns; the block then splits its patterns into
-        // 8 / nchp slices (nchp: nch rounded up to a power of two) and warp
+        // nch < FT_WARPS warps' columns; the block then splits its patterns into
+        // FT_WARPS / nchp slices (nchp: nch rounded up to a power of two) and warp
         // (c, s) scans column c against slice s, so that no warp idles
         // while there is work.
         const uint32_t nch = min((nw + 32u * G - 1u) / (32u * G), (uint32_t)FT_WARPS);
@@ -590,10 +594,12 @@ __global__ void __launch_bounds__(FT_THREADS, (ft_min_blocks<W, V, POS, FUSED>()
 // mma layout needs into one byte: thread t of a quad takes byte t, expanded
 // to eight FP8 values by a 256-entry table.  16-bit fingerprints use the
 // first 16 positions and leave the other 16 zero.
+constexpr int FM_THREADS = 256;  // the tensor-core filter keeps 8 warps per block
+constexpr int FM_WARPS = FM_THREADS / 32;
 constexpr int FM_TQ = 128;                       // patterns per tile: 8 row tiles of 16
 constexpr int FM_RT = FM_TQ / 16;
 constexpr int FM_GROUPS = 16;                    // groups of 8 words per warp and tile
-constexpr int FM_TW = FT_WARPS * FM_GROUPS * 8;  // 1024 words per tile
+constexpr int FM_TW = FM_WARPS * FM_GROUPS * 8;  // 1024 words per tile
 #ifndef FM_MIN_BLOCKS
 #define FM_MIN_BLOCKS 2
 #endif
@@ -606,16 +612,16 @@ __device__ __forceinline__ void mma_e4m3_f16(uint32_t &d0, uint32_t &d1, const u
 }
 
 template <int W, bool FUSED>
-__global__ void __launch_bounds__(FT_THREADS, FM_MIN_BLOCKS) k_filter_mma(FilterArgs A) {
+__global__ void __launch_bounds__(FM_THREADS, FM_MIN_BLOCKS) k_filter_mma(FilterArgs A) {
     __shared__ uint2 s_lut[256];  // byte -> eight E4M3 values (+1 for a set bit, -1 for a clear one)
     __shared__ uint32_t s_q[FM_TQ];
     __shared__ __align__(16) uint32_t s_w[FM_TW];
-    __shared__ uint64_t s_stage[FT_WARPS][FT_STAGE];
-    __shared__ uint32_t s_cnt[FT_WARPS];
+    __shared__ uint64_t s_stage[FM_WARPS][FT_STAGE];
+    __shared__ uint32_t s_cnt[FM_WARPS];
     __shared__ uint64_t s_tile;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 2, t = lane & 3;
-    for (int v = threadIdx.x; v < 256; v += FT_THREADS) {
+    for (int v = threadIdx.x; v < 256; v += FM_THREADS) {
         uint32_t lo = 0, hi = 0;
 #pragma unroll
         for (int i = 0; i < 4; i++) {
@@ -643,16 +649,16 @@ __global__ void __launch_bounds__(FT_THREADS, FM_MIN_BLOCKS) k_filter_mma(Filter
         const uint32_t nq = min((uint32_t)FM_TQ, S.q_count - qt * (uint32_t)FM_TQ);
         const uint32_t w0 = S.d_start + dt * (uint32_t)FM_TW;
         const uint32_t nw = min((uint32_t)FM_TW, S.d_count - dt * (uint32_t)FM_TW);
-        for (uint32_t j = threadIdx.x; j < (uint32_t)FM_TQ; j += FT_THREADS)
+        for (uint32_t j = threadIdx.x; j < (uint32_t)FM_TQ; j += FM_THREADS)
             s_q[j] = j < nq ? ((W == 32) ? A.qfp32[q0 + j] : (uint32_t)A.qfp16[q0 + j]) : 0u;
         if (W == 32) {
             // w0 is a multiple of 8 slots and the slack after the last bucket is
             // readable, so whole 128-bit vectors may be loaded past nw
-            for (uint32_t j = threadIdx.x; j * 4 < nw; j += FT_THREADS)
+            for (uint32_t j = threadIdx.x; j * 4 < nw; j += FM_THREADS)
                 *reinterpret_cast<uint4 *>(&s_w[4 * j]) = *reinterpret_cast<const uint4 *>(A.dfp + w0 + 4 * j);
         } else {
             const uint16_t *d16 = reinterpret_cast<const uint16_t *>(A.dfp);
-            for (uint32_t j = threadIdx.x; j < nw; j += FT_THREADS) s_w[j] = d16[w0 + j];
+            for (uint32_t j = threadIdx.x; j < nw; j += FM_THREADS) s_w[j] = d16[w0 + j];
         }
         __syncthreads();
         const int nr = (int)((nq + 15u) / 16u);
@@ -724,10 +730,10 @@ static int launch_mma(const FilterArgs &A, cudaStream_t st) {
     static int grid = 0;
     if (grid == 0) {
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_mma<W, FUSED>, FT_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_mma<W, FUSED>, FM_THREADS, 0);
         grid = sm_count() * (per_sm > 0 ? per_sm : 1);
     }
-    k_filter_mma<W, FUSED><<<grid, FT_THREADS, 0, st>>>(A);
+    k_filter_mma<W, FUSED><<<grid, FM_THREADS, 0, st>>>(A);
     FP_LAUNCHED(FUSED ? "k_filter_mma(fused)" : "k_filter_mma");
     return FP_OK;
 }
