@@ -431,12 +431,12 @@ int fp_query_ex(fp_index *ix, const uint8_t *chars, const int64_t *offsets, int6
     FilterCfg cfg{};
     cfg.mode = o.mode;
     // defaults from a sweep on the 1M-word English-like workload: 4 words per
-    // thread; 128 queries per tile with weight bands (narrower cell ranges
-    // per tile), 256 without
+    // thread; 96 queries per tile with weight bands (narrower cell ranges per
+    // tile; measured against 64 .. 256), 256 without
     cfg.v = o.words_per_thread == 8 ? 8 : 4;
     cfg.tq = o.mode == FP_MODE_PLAIN
                  ? 1
-                 : (o.tile_queries > 0 ? std::min(o.tile_queries, 256) : (ix->d_wstart != nullptr ? 128 : 256));
+                 : (o.tile_queries > 0 ? std::min(o.tile_queries, 256) : (ix->d_wstart != nullptr ? 96 : 256));
     cfg.k1mix = o.variant == 0 && k == 1;
     cfg.mma = o.variant == 2 && o.mode != FP_MODE_PLAIN;
     const bool fused = o.mode == FP_MODE_FUSED;
