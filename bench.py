@@ -518,7 +518,7 @@ def main():
         "config": {"workload": WORKLOAD, "fingerprint": f"{args.fp_type}32", "k": 1, "metrics": list(metrics),
                    "queries_per_step": n_q_step, "dictionary_words": len(w.dictionary),
                    "l2": "flushed between timed steps (256 MB write, outside the timed events)",
-                   "mode": "tiled filter with weight bands (96 queries per tile, 4 fingerprint words per "
+                   "mode": "tiled filter with weight bands (64 queries per tile, 4 fingerprint words per "
                            "thread), separate verify"},
         "pair_compares_per_s": world * pairs * args.steps / t_dev,
         "pairs_per_step": pairs, "pairs_tested_per_step": tested, "survivors_per_step": surv,

@@ -91,7 +91,7 @@ typedef enum {
 
 typedef struct {
     int32_t mode;            /* fp_mode; default FP_MODE_TILED */
-    int32_t tile_queries;    /* queries per block for FP_MODE_TILED / FUSED, 1..256; 0 = default (96 with
+    int32_t tile_queries;    /* queries per block for FP_MODE_TILED / FUSED, 1..256; 0 = default (64 with
                                 weight bands, i.e. all but position fingerprints; 256 for those) */
     int32_t words_per_thread;/* dictionary fingerprints per thread per tile, 4 or 8; 0 = default */
     int32_t variant;         /* 0 = automatic (k = 1: a quarter of the pair tests use an ALU-only

@@ -391,12 +391,14 @@ struct QueryRun {
     int32_t *d_err = nullptr;
     uint64_t *surv = nullptr, *matches = nullptr;
     int64_t surv_cap = 0, match_cap = 0;
+    uint8_t *plan_scratch = nullptr;
 };
 
 static void release_run(QueryRun &R, cudaStream_t st) {
     free_bucketed(&R.Q, st);
     if (R.plan.seg) cudaFreeAsync(R.plan.seg, st);
     if (R.plan.scal) cudaFreeAsync(R.plan.scal, st);
+    if (R.plan_scratch) cudaFreeAsync(R.plan_scratch, st);
     if (R.d_group) cudaFreeAsync(R.d_group, st);
     if (R.d_err) cudaFreeAsync(R.d_err, st);
     if (R.surv) cudaFreeAsync(R.surv, st);
@@ -431,12 +433,12 @@ int fp_query_ex(fp_index *ix, const uint8_t *chars, const int64_t *offsets, int6
     FilterCfg cfg{};
     cfg.mode = o.mode;
     // defaults from a sweep on the 1M-word English-like workload: 4 words per
-    // thread; 96 queries per tile with weight bands (narrower cell ranges per
-    // tile; measured against 64 .. 256), 256 without
+    // thread; 64 queries per tile with weight bands (narrower cell ranges per
+    // tile; measured against 96 .. 256), 256 without
     cfg.v = o.words_per_thread == 8 ? 8 : 4;
     cfg.tq = o.mode == FP_MODE_PLAIN
                  ? 1
-                 : (o.tile_queries > 0 ? std::min(o.tile_queries, 256) : (ix->d_wstart != nullptr ? 96 : 256));
+                 : (o.tile_queries > 0 ? std::min(o.tile_queries, 256) : (ix->d_wstart != nullptr ? 64 : 256));
     cfg.k1mix = o.variant == 0 && k == 1;
     cfg.mma = o.variant == 2 && o.mode != FP_MODE_PLAIN;
     const bool fused = o.mode == FP_MODE_FUSED;
@@ -508,6 +510,11 @@ int fp_query_ex(fp_index *ix, const uint8_t *chars, const int64_t *offsets, int6
     }
     CK(cudaMallocAsync((void **)&R.plan.seg, sizeof(Segment) * (size_t)R.plan.max_segments, st));
     CK(cudaMallocAsync((void **)&R.plan.scal, 8 * sizeof(uint64_t), st));
+    if (band) {  // the planner's scratch: one thread per tile of patterns
+        const int64_t ucap = (n_queries + tq - 1) / tq + R.Q.nbins;
+        CK(cudaMallocAsync((void **)&R.plan_scratch, plan_scratch_bytes(ucap, R.Q.nbins), st));
+        plan_scratch_place(&R.plan, R.plan_scratch, ucap, R.Q.nbins);
+    }
     TRY(plan_segments(R.Q, ix->D, R.d_group, R.d_group + 1, tq, tw, &R.plan, st, band ? ix->d_wstart : nullptr,
                       ix->P.width));
     // survivor capacity: exact pair count when the host saw the lengths, else a bound

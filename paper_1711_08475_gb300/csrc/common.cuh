@@ -148,7 +148,18 @@ struct QueryPlan {
     // device scalars (one small block)
     uint64_t *scal = nullptr;   // [0] n_segments [1] total tiles [2] pairs [3] tile counter
                                 // [4] survivors [5] matches [6] plan overflow [7] pairs tested
+    // scratch of the banded planner over many blocks (optional: without it one
+    // block plans); units_cap >= ceil(patterns / tq) + bins
+    int32_t units_cap = 0;
+    int32_t *unit0 = nullptr;     // [bins + 1] first unit of every bin
+    int32_t *u_seg = nullptr;     // [units_cap] segments per unit, then their offsets
+    uint64_t *u_tiles = nullptr;  // [units_cap] tiles per unit, then their offsets
+    uint64_t *acc = nullptr;      // [4] pairs, tested pairs, fall-back flag, units
 };
+// Bytes of the banded planner's scratch for a plan of units_cap units over nbins
+// bins, and the scratch placed at base (256-byte aligned).
+size_t plan_scratch_bytes(int64_t units_cap, int nbins);
+void plan_scratch_place(QueryPlan *plan, uint8_t *base, int64_t units_cap, int nbins);
 
 struct FilterCfg {
     int mode;      // fp_mode

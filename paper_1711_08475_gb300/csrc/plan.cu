@@ -62,6 +62,9 @@ size_t pipe_layout(const PipeShape &s, uint8_t *base, Pipe *p) {
     // tile of 64 patterns (three lengths, several runs of cells each) -- a
     // plan that needs more falls back to whole buckets on the device
     const int64_t seg_cap = std::min<int64_t>(0x7FFFFFFF, std::max<int64_t>(nbins * 31, (n / 64 + nbins) * 40));
+    // the banded planner's scratch, for tiles of 32 patterns or more (smaller
+    // tiles plan whole buckets)
+    const int64_t units_cap = std::min<int64_t>(0x7FFFFFFF, n / 32 + nbins);
     size_t off = 0;
     const size_t o_chars = carve(off, (size_t)s.chars + 16), o_off = carve(off, 8 * (size_t)(n + 1)),
                  o_bs = carve(off, 8 * (size_t)(s.batches + 1)), o_bg = carve(off, 4 * (size_t)s.batches),
@@ -73,6 +76,7 @@ size_t pipe_layout(const PipeShape &s, uint8_t *base, Pipe *p) {
                  o_k2 = carve(off, 8 * (size_t)n), o_hist = carve(off, 4 * (size_t)nbins),
                  o_ust = carve(off, 4 * (size_t)nbins), o_s16 = carve(off, 8 * (size_t)nbins),
                  o_tot = carve(off, 16), o_seg = carve(off, sizeof(Segment) * (size_t)seg_cap),
+                 o_pls = carve(off, plan_scratch_bytes(units_cap, (int)nbins)),
                  o_scal = carve(off, 8 * 8), o_err = carve(off, 4), o_row = carve(off, 8 * (size_t)(n + 1)),
                  o_m = carve(off, 8 * (size_t)cap), o_t = carve(off, 8 * (size_t)cap),
                  o_idx = carve(off, 4 * (size_t)cap), o_rh = carve(off, 4 * (size_t)rh);
@@ -100,6 +104,7 @@ size_t pipe_layout(const PipeShape &s, uint8_t *base, Pipe *p) {
         p->S.radix_hist = (uint32_t *)(base + o_rh);
         p->qp.seg = (Segment *)(base + o_seg);
         p->seg_cap = (int32_t)seg_cap;
+        plan_scratch_place(&p->qp, base + o_pls, units_cap, (int)nbins);
         p->qp.scal = (uint64_t *)(base + o_scal);
         p->d_err = (int32_t *)(base + o_err);
         p->row_ptr = (int64_t *)(base + o_row);

@@ -38,10 +38,10 @@ struct PlanCounts {
 };
 
 constexpr int PLAN_MAX_BINS = 8192;  // 32 (k, metric) groups x 256 lengths
-constexpr int PLAN_CHUNK = 6;
+constexpr int PLAN_CHUNK = 6;  // table loads a planner thread keeps in flight per length
 #ifndef PLAN_MERGE_GAP
 #define PLAN_MERGE_GAP 0u  // runs closer than this many slots are merged (the gap's words are tested too)
-#endif  // table loads a planner thread keeps in flight per length
+#endif
 
 __device__ __forceinline__ int slot_cell_of(const void *fp, int width, uint32_t s) {
     return fp_cell(width == 16 ? (uint32_t)((const uint16_t *)fp)[s] : ((const uint32_t *)fp)[s], width);
@@ -162,13 +162,15 @@ __device__ void plan_unit(int c, int64_t u, const int32_t *__restrict__ qb_start
 // One block of 1024 threads.  The units (bins, or tiles of bins with weight
 // bands) are numbered bin by bin; thread t plans units [t U / 1024,
 // (t + 1) U / 1024): a counting pass, a block scan of the segment and tile
-// counts, and a writing pass.
+// counts, and a writing pass.  only_if (optional): plan only when *only_if is
+// set (the parallel banded planner's fall-back to whole buckets).
 __global__ void __launch_bounds__(1024) k_plan_segments(
     const int32_t *__restrict__ qb_start, const int32_t *__restrict__ qb_count, int q_nbins,
     const int32_t *__restrict__ db_start, const int32_t *__restrict__ db_count,
     const int32_t *__restrict__ group_k, const int32_t *__restrict__ group_metric, int tq, int tw, const void *q_fp,
     int width, const int32_t *__restrict__ d_wstart, Segment *__restrict__ seg, int max_segments,
-    uint64_t *__restrict__ scal) {
+    uint64_t *__restrict__ scal, const uint64_t *only_if) {
+    if (only_if && *only_if == 0) return;  // block-uniform
     __shared__ int32_t s_unit0[PLAN_MAX_BINS + 1];  // first unit of every bin
     __shared__ int32_t s_n[1024];
     __shared__ uint64_t s_t[1024];
@@ -271,12 +273,200 @@ __global__ void __launch_bounds__(1024) k_plan_segments(
     }
 }
 
+// ---------------------------------------------------------------------------
+// the banded planner over many blocks
+// ---------------------------------------------------------------------------
+// One thread per unit (tile of patterns), so that the chains of table loads of
+// different tiles run on the whole GPU instead of one block:
+//   k_plan_prefix  (1 block)  first unit of every bin, unit count
+//   k_plan_units   (a thread per unit) segments and tiles per unit, pair sums
+//   k_plan_offsets (1 block)  exclusive prefix of both, the counters
+//   k_plan_units   again, writing each unit's segments at its offsets
+// acc: [0] eligible pairs, [1] tested pairs, [2] fall-back flag (the units or
+// the segments do not fit: k_plan_segments then plans whole buckets), [3] U.
+__global__ void __launch_bounds__(1024) k_plan_prefix(const int32_t *__restrict__ qb_count, int nbins, int tq,
+                                                      int32_t *__restrict__ unit0, uint64_t *__restrict__ acc,
+                                                      int units_cap) {
+    __shared__ uint64_t s_t[1024];
+    const int t = threadIdx.x, per = (nbins + 1023) / 1024;
+    const int lo = min(nbins, t * per), hi = min(nbins, lo + per);
+    uint64_t a = 0;
+    for (int c = lo; c < hi; c++) a += (uint64_t)plan_units(qb_count[c], true, tq);
+    s_t[t] = a;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const uint64_t v = t >= o ? s_t[t - o] : 0;
+        __syncthreads();
+        s_t[t] += v;
+        __syncthreads();
+    }
+    const uint64_t U = s_t[1023];
+    const bool fits = U <= (uint64_t)units_cap;
+    uint64_t r = s_t[t] - a;
+    for (int c = lo; c < hi; c++) {
+        unit0[c] = fits ? (int32_t)r : 0;
+        r += (uint64_t)plan_units(qb_count[c], true, tq);
+    }
+    if (t == 0) {
+        unit0[nbins] = fits ? (int32_t)U : 0;
+        acc[0] = 0;
+        acc[1] = 0;
+        acc[2] = fits ? 0 : 1;
+        acc[3] = fits ? U : 0;
+    }
+}
+
+template <bool WRITE>
+__global__ void __launch_bounds__(128) k_plan_units(
+    const int32_t *__restrict__ qb_start, const int32_t *__restrict__ qb_count, int nbins,
+    const int32_t *__restrict__ db_start, const int32_t *__restrict__ db_count,
+    const int32_t *__restrict__ group_k, const int32_t *__restrict__ group_metric, int tq, int tw, const void *q_fp,
+    int width, const int32_t *__restrict__ d_wstart, Segment *__restrict__ seg, int max_segments,
+    const int32_t *__restrict__ unit0, int32_t *__restrict__ u_seg, uint64_t *__restrict__ u_tiles,
+    uint64_t *__restrict__ acc) {
+    __shared__ unsigned long long s_sum[2];
+    const bool fallback = acc[2] != 0;
+    const int64_t U = (int64_t)acc[3];
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (!WRITE && threadIdx.x < 2) s_sum[threadIdx.x] = 0;
+    if (!WRITE) __syncthreads();
+    PlanCounts pc;
+    if (!fallback && u < U) {
+        int lo = 0, hi = nbins - 1;  // bin of the unit: the last bin whose first unit is <= u
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (unit0[mid] <= u) lo = mid;
+            else hi = mid - 1;
+        }
+        int64_t si = WRITE ? (int64_t)u_seg[u] : 0;
+        uint64_t tb = WRITE ? u_tiles[u] : 0;
+        plan_unit<WRITE>(lo, u - unit0[lo], qb_start, qb_count, db_start, db_count, group_k, group_metric, tq, tw,
+                         q_fp, width, d_wstart, true, seg, max_segments, si, tb, pc);
+        if (!WRITE) {
+            u_seg[u] = pc.nseg;
+            u_tiles[u] = pc.tiles;
+        }
+    }
+    if (!WRITE) {
+        unsigned long long p = pc.pairs, x = pc.tested;
+        for (int o = 16; o > 0; o >>= 1) {
+            p += __shfl_down_sync(0xffffffffu, p, o);
+            x += __shfl_down_sync(0xffffffffu, x, o);
+        }
+        if ((threadIdx.x & 31) == 0 && (p | x)) {
+            atomicAdd(&s_sum[0], p);
+            atomicAdd(&s_sum[1], x);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && (s_sum[0] | s_sum[1])) {
+            atomicAdd((unsigned long long *)&acc[0], s_sum[0]);
+            atomicAdd((unsigned long long *)&acc[1], s_sum[1]);
+        }
+    }
+}
+
+// Exclusive prefix of the segments and tiles per unit, in place (one block;
+// thread t takes a contiguous run of units), then the plan's counters.
+__global__ void __launch_bounds__(1024) k_plan_offsets(int32_t *__restrict__ u_seg, uint64_t *__restrict__ u_tiles,
+                                                       uint64_t *__restrict__ acc, int max_segments,
+                                                       uint64_t *__restrict__ scal) {
+    __shared__ int64_t s_n[1024];
+    __shared__ uint64_t s_t[1024];
+    if (acc[2] != 0) return;  // block-uniform: the fall-back planner writes the counters
+    const int t = threadIdx.x;
+    const int64_t U = (int64_t)acc[3], per = (U + 1023) / 1024;
+    const int64_t lo = min(U, t * per), hi = min(U, lo + per);
+    int64_t n = 0;
+    uint64_t ti = 0;
+    for (int64_t u = lo; u < hi; u++) {
+        n += u_seg[u];
+        ti += u_tiles[u];
+    }
+    s_n[t] = n;
+    s_t[t] = ti;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const int64_t a = t >= o ? s_n[t - o] : 0;
+        const uint64_t b = t >= o ? s_t[t - o] : 0;
+        __syncthreads();
+        s_n[t] += a;
+        s_t[t] += b;
+        __syncthreads();
+    }
+    const int64_t ns = s_n[1023];
+    if (ns > max_segments) {  // does not fit: plan whole buckets instead
+        if (t == 0) acc[2] = 1;
+        return;
+    }
+    int64_t rn = s_n[t] - n;
+    uint64_t rt = s_t[t] - ti;
+    for (int64_t u = lo; u < hi; u++) {
+        const int32_t a = u_seg[u];
+        const uint64_t b = u_tiles[u];
+        u_seg[u] = (int32_t)rn;
+        u_tiles[u] = rt;
+        rn += a;
+        rt += b;
+    }
+    if (t == 1023) {
+        scal[0] = (uint64_t)ns;
+        scal[1] = s_t[1023];
+        scal[2] = acc[0];
+        scal[3] = 0;
+        scal[4] = 0;
+        scal[5] = 0;
+        scal[6] = 0;
+        scal[7] = acc[1];
+    }
+}
+
+static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+size_t plan_scratch_bytes(int64_t units_cap, int nbins) {
+    return al256(4 * (size_t)(nbins + 1)) + al256(4 * (size_t)units_cap) + al256(8 * (size_t)units_cap) + al256(32);
+}
+
+void plan_scratch_place(QueryPlan *plan, uint8_t *base, int64_t units_cap, int nbins) {
+    size_t off = 0;
+    plan->units_cap = (int32_t)units_cap;
+    plan->unit0 = (int32_t *)(base + off);
+    off += al256(4 * (size_t)(nbins + 1));
+    plan->u_seg = (int32_t *)(base + off);
+    off += al256(4 * (size_t)units_cap);
+    plan->u_tiles = (uint64_t *)(base + off);
+    off += al256(8 * (size_t)units_cap);
+    plan->acc = (uint64_t *)(base + off);
+}
+
 int plan_segments(const Bucketed &q, const Bucketed &d, const int32_t *d_group_k,
                   const int32_t *d_group_metric, int tq, int tw, QueryPlan *plan, cudaStream_t st,
                   const int32_t *d_wstart, int width) {
+    if (d_wstart && plan->unit0 && plan->units_cap > 0) {
+        const unsigned blocks = (unsigned)((plan->units_cap + 127) / 128);
+        k_plan_prefix<<<1, 1024, 0, st>>>(q.b_count, q.nbins, tq, plan->unit0, plan->acc, plan->units_cap);
+        FP_LAUNCHED("k_plan_prefix");
+        k_plan_units<false><<<blocks, 128, 0, st>>>(q.b_start, q.b_count, q.nbins, d.b_start, d.b_count, d_group_k,
+                                                    d_group_metric, tq, tw, q.fp, width, d_wstart, plan->seg,
+                                                    plan->max_segments, plan->unit0, plan->u_seg, plan->u_tiles,
+                                                    plan->acc);
+        FP_LAUNCHED("k_plan_units");
+        k_plan_offsets<<<1, 1024, 0, st>>>(plan->u_seg, plan->u_tiles, plan->acc, plan->max_segments, plan->scal);
+        FP_LAUNCHED("k_plan_offsets");
+        k_plan_units<true><<<blocks, 128, 0, st>>>(q.b_start, q.b_count, q.nbins, d.b_start, d.b_count, d_group_k,
+                                                   d_group_metric, tq, tw, q.fp, width, d_wstart, plan->seg,
+                                                   plan->max_segments, plan->unit0, plan->u_seg, plan->u_tiles,
+                                                   plan->acc);
+        FP_LAUNCHED("k_plan_units");
+        // whole buckets, only when the banded plan did not fit
+        k_plan_segments<<<1, 1024, 0, st>>>(q.b_start, q.b_count, q.nbins, d.b_start, d.b_count, d_group_k,
+                                            d_group_metric, tq, tw, nullptr, width, nullptr, plan->seg,
+                                            plan->max_segments, plan->scal, plan->acc + 2);
+        FP_LAUNCHED("k_plan_segments");
+        return FP_OK;
+    }
     k_plan_segments<<<1, 1024, 0, st>>>(q.b_start, q.b_count, q.nbins, d.b_start, d.b_count, d_group_k,
                                         d_group_metric, tq, tw, d_wstart ? q.fp : nullptr, width, d_wstart, plan->seg,
-                                        plan->max_segments, plan->scal);
+                                        plan->max_segments, plan->scal, nullptr);
     FP_LAUNCHED("k_plan_segments");
     return FP_OK;
 }

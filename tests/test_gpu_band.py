@@ -164,7 +164,7 @@ def test_band_after_new_symbol_map(fp):
     rp, idx = r.csr()
     assert np.array_equal(rp, rp0) and np.array_equal(idx, idx0)
     st = r.stats()
-    assert st["pairs_tested"] == expected_tested(d, q, 1, "lev", ix.symbol_map(), "occ", 16, 96)  # default tile
+    assert st["pairs_tested"] == expected_tested(d, q, 1, "lev", ix.symbol_map(), "occ", 16, 64)  # default tile
     _, _, _, surv = oracle.filter_match(d, q, 1, "lev", ix.symbol_map(), "occ", 16, gray=True)
     assert st["survivors"] == surv
 
