@@ -184,3 +184,32 @@ def test_band_at_scale(fp, metric):
         assert np.array_equal(rp, rp0) and np.array_equal(idx, idx0)
         assert st["pairs_tested"] == expected_tested(d, q, 1, metric, m, "count", 32, tq)
         assert st["pairs_tested"] < 0.95 * st["pairs"]
+
+
+def test_batched_plan_falls_back_to_whole_buckets(fp):
+    """The batched pipeline's planner scratch holds tiles of 32 patterns or
+    more; with one pattern per tile the banded plan does not fit and the device
+    plans whole buckets instead: every eligible pair is tested, the answers
+    stay the oracle's.  With 64 per tile the bands apply."""
+    w = datagen.english1m(20000, 4000)
+    ix = fp.fp_build(w.dictionary, fp_type="count", width=32)
+    parts, spec = [], []
+    for metric, k, n in (("lev", 1, 3000), ("ham", 1, 2500), ("lev", 2, 700)):
+        parts.append(w.queries[metric].subset(np.arange(n)))
+        spec.append((n, k, metric))
+    Q = datagen.Strings.concat(parts)
+    for tq, banded in ((1, False), (64, True)):
+        res = fp.fp_query_batched(ix, Q, batches=spec, tile_queries=tq)
+        st = res.stats()
+        if banded:
+            assert st["pairs_tested"] < st["pairs"]
+        else:
+            assert st["pairs_tested"] == st["pairs"]
+        rp, idx = res.csr()
+        base = 0
+        for (n, k, metric) in spec:
+            sub = Q.subset(np.arange(base, base + n))
+            rp0, idx0 = oracle.match(w.dictionary, sub, k, metric)
+            assert np.array_equal(rp[base:base + n + 1] - rp[base], rp0), (tq, n, k, metric)
+            assert np.array_equal(idx[rp[base]:rp[base + n]], idx0), (tq, n, k, metric)
+            base += n
