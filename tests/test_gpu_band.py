@@ -187,14 +187,15 @@ def test_band_at_scale(fp, metric):
 
 
 def test_batched_plan_falls_back_to_whole_buckets(fp):
-    """The batched pipeline's planner scratch holds tiles of 32 patterns or
-    more; with one pattern per tile the banded plan does not fit and the device
-    plans whole buckets instead: every eligible pair is tested, the answers
-    stay the oracle's.  With 64 per tile the bands apply."""
-    w = datagen.english1m(20000, 4000)
+    """The batched pipeline's planner scratch holds n / 32 + bins tiles (bins:
+    256 per (k, metric) group the run may hold, 32 groups); 12,000 patterns at
+    one pattern per tile need more, so the device plans whole buckets instead:
+    every eligible pair is tested, the answers stay the oracle's.  With 64 per
+    tile the bands apply."""
+    w = datagen.english1m(20000, 6000)
     ix = fp.fp_build(w.dictionary, fp_type="count", width=32)
     parts, spec = [], []
-    for metric, k, n in (("lev", 1, 3000), ("ham", 1, 2500), ("lev", 2, 700)):
+    for metric, k, n in (("lev", 1, 5000), ("ham", 1, 5000), ("lev", 2, 2000)):
         parts.append(w.queries[metric].subset(np.arange(n)))
         spec.append((n, k, metric))
     Q = datagen.Strings.concat(parts)
