@@ -89,9 +89,16 @@ __device__ __forceinline__ void flush_matches(const VerifyArgs &A, uint64_t *sta
 #ifndef VERIFY_MIN_BLOCKS
 #define VERIFY_MIN_BLOCKS 4  // measured against 1 and 3 (Hamming keeps 64 registers instead of 80)
 #endif
+#ifndef VERIFY_LEV1_MIN_BLOCKS
+#define VERIFY_LEV1_MIN_BLOCKS 4  // the direct k = 1 test: 48 registers; 6 and 8 blocks measured no faster
+#endif
+template <int METRIC, int K>
+constexpr int verify_min_blocks() {
+    return METRIC == FP_LEV && K == 1 ? VERIFY_LEV1_MIN_BLOCKS : VERIFY_MIN_BLOCKS;
+}
 
 template <int METRIC, int K>
-__global__ void __launch_bounds__(256, VERIFY_MIN_BLOCKS) k_verify(VerifyArgs A, int k) {
+__global__ void __launch_bounds__(256, (verify_min_blocks<METRIC, K>())) k_verify(VerifyArgs A, int k) {
     constexpr int U = VERIFY_U;
     __shared__ uint64_t s_stage[8][VSTAGE];
     __shared__ uint32_t s_cnt[8];
