@@ -530,7 +530,11 @@ def main():
                      "filter_ms_per_launch": filt_launch_ms,
                      "peak_basis": f"{sms} SMs x {mhz:.0f} MHz (sampled) x min(POPC {r_popc:.1f}, "
                                    f"LOP3 {r_lop:.1f}/2) per clock per SM (probe-measured unit rates)",
-                     "probe_pair_tests_per_clk_per_sm": probe[0]["ops_per_clk_per_sm"]},
+                     "probe_pair_tests_per_clk_per_sm": probe[0]["ops_per_clk_per_sm"],
+                     # the same launches counted in eligible pairs decided (tested by the
+                     # kernel, or rejected by the weight bands without a test)
+                     "eligible_pairs_decided_per_s": pairs / (filt_ms / 1e3),
+                     "eligible_frac": pairs / (filt_ms / 1e3) / peak},
         "gpu_launches": launches,
         "clocks": clocks,
     }
