@@ -19,6 +19,9 @@ namespace fpk {
 namespace {
 
 constexpr int RB_THREADS = 256;
+#ifndef RADIX_MID_BLOCKS
+#define RADIX_MID_BLOCKS 256  // blocks per pass below 2^26 keys (measured against 64 and 128)
+#endif
 constexpr int RB_WARPS = RB_THREADS / 32;
 
 __device__ __forceinline__ void block_range(uint64_t n, int nb, int b, uint64_t *lo, uint64_t *hi) {
@@ -191,7 +194,7 @@ int radix_sort_u64(uint64_t *keys, uint64_t *tmp, const uint64_t *d_n, int64_t m
     *result = keys;
     if (max_n <= 0 || bits_hi <= bits_lo) return FP_OK;
     int64_t nb64 = (max_n + 4095) / 4096;
-    const int64_t cap = max_n >= (1LL << 26) ? 4096 : 256;  // more blocks only for very large sorts
+    const int64_t cap = max_n >= (1LL << 26) ? 4096 : RADIX_MID_BLOCKS;  // more blocks only for very large sorts
     int nb = (int)(nb64 < 1 ? 1 : (nb64 > cap ? cap : nb64));
     uint32_t *hist = nullptr;
     FP_CUDA(cudaMallocAsync((void **)&hist, sizeof(uint32_t) * 256 * (size_t)nb, st));
@@ -240,7 +243,7 @@ namespace fpk {
 // holds 256 entries per block).
 int radix_blocks(int64_t max_n) {
     int64_t nb64 = (max_n + 4095) / 4096;
-    const int64_t cap = max_n >= (1LL << 26) ? 4096 : 256;  // more blocks only for very large sorts
+    const int64_t cap = max_n >= (1LL << 26) ? 4096 : RADIX_MID_BLOCKS;  // more blocks only for very large sorts
     return (int)(nb64 < 1 ? 1 : (nb64 > cap ? cap : nb64));
 }
 
