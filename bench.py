@@ -256,6 +256,40 @@ def same_csr(a, b) -> bool:
     return np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
 
 
+def combined_leg(fp, w, ix, dev, metrics, stream, flush, step_device, args):
+    """The headline step with combined types (count32 + occ32 over the 32 most
+    frequent symbols; a pair survives only if both pass Eq. 1) against the
+    same step with count32 alone: same patterns, identical match lists."""
+    ixc = fp.fp_build(w.dictionary, fp_type="count", width=32, combined=True)
+
+    def step_c():  # the same work as the headline step (stats only, no copies)
+        out = []
+        for m in metrics:
+            r = fp.fp_query_ex(ixc, dev[m][0], dev[m][1], k=1, metric=m, variant=args.variant)
+            out.append(r.stats())
+            r.free()
+        return out
+
+    reps = max(5, args.steps // 5)
+    ms_c, out_c = timed(step_c, stream, flush, reps)
+    ms_1, _ = timed(step_device, stream, flush, reps)
+    same = True
+    for m in metrics:  # answers compared outside the timed steps
+        rc_ = fp.fp_query_ex(ixc, dev[m][0], dev[m][1], k=1, metric=m, variant=args.variant)
+        r = fp.fp_query_ex(ix, dev[m][0], dev[m][1], k=1, metric=m, variant=args.variant)
+        same &= same_csr(rc_.csr(), r.csr())
+        r.free()
+        rc_.free()
+    surv = sum(st["survivors"] for st in out_c)
+    stage = {k: sum(st[k] for st in out_c) for k in ("ms_prepare", "ms_filter", "ms_verify", "ms_emit", "ms_total")}
+    ixc.free()
+    n = sum(len(w.queries[m]) for m in metrics)
+    return {"fingerprints": "count32 + occ32 (combined types)", "queries_per_s": n / (ms_c / 1e3),
+            "ms_per_step": ms_c, "count32_alone_ms_per_step": ms_1, "survivors_per_step": surv,
+            "stage_ms_per_step": stage, "identical_to_count32": bool(same),
+            "timing": f"mean of {reps} steps, L2 flushed before each, CUDA events"}
+
+
 def url_legs(fp, torch, args, stream, flush):
     """The learned map and the serving loop on URL-like strings (k = 1, Lev).
 
@@ -566,6 +600,8 @@ def main():
             import oracle
             oracle.build()
             result["cpu_baseline"] = cpu_baseline(w, args.cpu_sample)
+        if rank == 0 and args.fp_type == "count":
+            result["combined_types"] = combined_leg(fp, w, ix, dev, metrics, stream, flush, step_device, args)
         if not args.no_url and rank == 0:
             result.update(url_legs(fp, torch, args, stream, flush))
         if not args.no_batched and rank == 0:

@@ -78,7 +78,12 @@ typedef struct {
     int32_t set;               /* fp_symset; default FP_SET_COMMON */
     int32_t count_bits;        /* b for FP_COUNT, 1..8; 0 = default 2 (Sec. 4) */
     int32_t pos_bits;          /* p for FP_POS, 1..8; 0 = default 3 (Sec. 4) */
-    int32_t reserved;
+    int32_t combined;          /* 1: combined types (occurrence + count in 64 bits): every word and
+                                  pattern also gets a 32-bit occurrence fingerprint over the 32 most
+                                  frequent symbols, and a pair survives only if both fingerprints
+                                  pass Eq. 1 (each is sound alone, Theorem 1).  FP_COUNT at 32 bits
+                                  only; used by fp_query / fp_query_ex (batched runs, the server and
+                                  fp_query_noalloc test the count fingerprint alone).  0 = off */
     const int8_t *custom_map;  /* host, [256]: field of each byte value or -1; only for FP_SET_CUSTOM */
 } fp_build_opts;
 

@@ -162,7 +162,7 @@ class Index:
 
 
 def fp_build(chars, offsets=None, fp_type: str = "occ", width: int = 32, symbol_set: str = "common",
-             count_bits: int = 2, pos_bits: int = 3, custom_map=None, stream=None) -> Index:
+             count_bits: int = 2, pos_bits: int = 3, custom_map=None, stream=None, combined: bool = False) -> Index:
     """Builds the resident index (fp_build in include/fp.h)."""
     L = load()
     chars, offsets, n = _strings(chars, offsets)
@@ -170,6 +170,7 @@ def fp_build(chars, offsets=None, fp_type: str = "occ", width: int = 32, symbol_
     o.set = SETS[symbol_set] if custom_map is None else FP_SET_CUSTOM
     o.count_bits = count_bits
     o.pos_bits = pos_bits
+    o.combined = 1 if combined else 0
     keep = None
     if custom_map is not None:
         keep = np.ascontiguousarray(custom_map, dtype=np.int8)

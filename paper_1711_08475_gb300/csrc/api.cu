@@ -230,6 +230,9 @@ int fp_build(const uint8_t *chars, const int64_t *offsets, int64_t n_words, int 
     int rc = make_params(type, width_bits, o.count_bits, o.pos_bits, &P);
     if (rc != FP_OK) return fail(rc, "fingerprint type / width / b / p not supported");
     if (o.set < FP_SET_COMMON || o.set > FP_SET_CUSTOM) return fail(FP_E_INVAL, "bad symbol set");
+    if (o.combined != 0 && o.combined != 1) return fail(FP_E_INVAL, "combined must be 0 or 1");
+    if (o.combined && (type != FP_COUNT || width_bits != 32))
+        return fail(FP_E_UNSUPPORTED, "combined types: count fingerprints of 32 bits only");
     if (o.set == FP_SET_CUSTOM) {
         if (!o.custom_map) return fail(FP_E_INVAL, "custom map is null");
         for (int c = 0; c < 256; c++)
@@ -278,6 +281,20 @@ int fp_build(const uint8_t *chars, const int64_t *offsets, int64_t n_words, int 
         rc = weight_order(&ix->D, P, ix->d_wstart, st);
         if (rc != FP_OK) goto fail_out;
     }
+    if (o.combined) {  // the second fingerprint: occurrence over the 32 most frequent symbols
+        if (cudaMalloc((void **)&ix->d_map2, 256) != cudaSuccess) {
+            rc = cuda_fail(cudaGetLastError(), "second map");
+            goto fail_out;
+        }
+        if ((rc = make_params(FP_OCC, 32, 0, 0, &ix->P2)) != FP_OK ||
+            (rc = symbol_map(S.chars, S.total, FP_SET_COMMON, ix->P2.sigma, ix->d_map2, ix->d_counts, st)) != FP_OK ||
+            (rc = second_fingerprints(&ix->D, ix->d_map2, ix->P2, st)) != FP_OK)
+            goto fail_out;
+        if (cudaMemcpyAsync(ix->h_map2, ix->d_map2, 256, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+            rc = cuda_fail(cudaGetLastError(), "second map copy");
+            goto fail_out;
+        }
+    }
     {
         cudaError_t e;
         if ((e = cudaMemcpyAsync(ix->h_count, ix->D.b_count, sizeof(ix->h_count), cudaMemcpyDeviceToHost, st)) !=
@@ -299,7 +316,8 @@ int fp_build(const uint8_t *chars, const int64_t *offsets, int64_t n_words, int 
         goto fail_out;
     }
     ix->device_bytes = ix->D.n_slots * (4 + 1 + 4) + (ix->D.n_slots + FP_SLACK_SLOTS) * (P.width / 8) +
-                       ix->D.str_bytes + STR_SLACK + 256 * 9;
+                       ix->D.str_bytes + STR_SLACK + 256 * 9 + (ix->D.fp2 ? ix->D.n_slots * 4 + 256 : 0) +
+                       (ix->d_wstart ? 256 * 4 * (int64_t)(cell_count(P.width) + 1) : 0);
     S.release(st);
     cudaFreeAsync(d_err, st);
     cudaStreamSynchronize(st);
@@ -319,6 +337,7 @@ void fp_free(fp_index *ix) {
     if (ix->d_map) cudaFree(ix->d_map);
     if (ix->d_counts) cudaFree(ix->d_counts);
     if (ix->d_wstart) cudaFree(ix->d_wstart);
+    if (ix->d_map2) cudaFree(ix->d_map2);
     delete ix;
 }
 
@@ -352,6 +371,7 @@ int fp_set_symbol_map(fp_index *ix, const int8_t *map) {
     ix->set = FP_SET_CUSTOM;
     FP_TRY(refingerprint(&ix->D, ix->d_map, ix->P, 0));
     if (ix->d_wstart) FP_TRY(weight_order(&ix->D, ix->P, ix->d_wstart, 0));  // the weights changed with the map
+    if (ix->d_map2) FP_TRY(second_fingerprints(&ix->D, ix->d_map2, ix->P2, 0));  // the slots moved
     FP_CUDA(cudaDeviceSynchronize());
     return FP_OK;
 }
@@ -497,6 +517,7 @@ int fp_query_ex(fp_index *ix, const uint8_t *chars, const int64_t *offsets, int6
     }
     CK(cudaMemsetAsync(R.d_err, 0, sizeof(int32_t), st));
     TRY(bucketize(S.chars, S.off, n_queries, S.total, nullptr, 1, ix->d_map, ix->P, true, st, &R.Q, R.d_err, band));
+    if (ix->d_map2) TRY(second_fingerprints(&R.Q, ix->d_map2, ix->P2, st));  // combined types
     // weight bands: patterns in cell order; per tile of tq patterns and
     // dictionary bucket a few runs of cells (at most one per admissible
     // (x, y)); a plan that needs more than 32 per (tile, bucket) on average

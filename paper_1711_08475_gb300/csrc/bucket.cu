@@ -406,7 +406,7 @@ int fingerprint_list(const uint8_t *d_chars, const int64_t *d_off, int64_t n, co
 }
 
 void free_bucketed(Bucketed *b, cudaStream_t st) {
-    void *ptrs[] = {b->fp, b->idx, b->len, b->row16, b->str, b->b_start, b->b_count};
+    void *ptrs[] = {b->fp, b->idx, b->len, b->row16, b->str, b->b_start, b->b_count, b->fp2};
     for (void *p : ptrs) {
         if (!p) continue;
         if (b->stream_ordered) cudaFreeAsync(p, st);
@@ -702,6 +702,40 @@ fail:
     if (tot) cudaFreeAsync(tot, st);
     free_bucketed(&B, st);
     return rc;
+}
+
+// Combined types: the 32-bit occurrence fingerprint of every real slot from
+// its row (padding slots get 0).
+__global__ void __launch_bounds__(256) k_second_fp(Bucketed B, const int8_t *__restrict__ map, FpParams P) {
+    __shared__ int8_t smap[256];
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) smap[t] = map[t];
+    __syncthreads();
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < B.n_slots;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t f = 0;
+        if (B.idx[s] >= 0) {
+            const int L = B.len[s];
+            const uint8_t *row = B.str + (uint64_t)B.row16[s] * 16;
+            FpAcc<FP_OCC> acc;
+            acc.init(P);
+            for (int i = 0; i < L; i++) acc.add(smap[row[i]], i, L, P);
+            f = acc.finish(P);
+        }
+        B.fp2[s] = f;
+    }
+}
+
+int second_fingerprints(Bucketed *B, const int8_t *d_map2, const FpParams &P2, cudaStream_t st) {
+    if (!B->fp2) {
+        const size_t bytes = sizeof(uint32_t) * (size_t)(B->n_slots > 0 ? B->n_slots : 1);
+        const cudaError_t e = B->stream_ordered ? cudaMallocAsync((void **)&B->fp2, bytes, st)
+                                                : cudaMalloc((void **)&B->fp2, bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "second fingerprints");
+    }
+    if (B->n_slots <= 0) return FP_OK;
+    k_second_fp<<<grid_for(B->n_slots, 256, 8192), 256, 0, st>>>(*B, d_map2, P2);
+    FP_LAUNCHED("k_second_fp");
+    return FP_OK;
 }
 
 int refingerprint(Bucketed *B, const int8_t *d_map, const FpParams &P, cudaStream_t st) {

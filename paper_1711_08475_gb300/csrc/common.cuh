@@ -74,6 +74,7 @@ struct Bucketed {
     int64_t str_bytes = 0;  // bytes of padded rows
     // device arrays
     void *fp = nullptr;         // uint16 or uint32 per slot (+ FP_SLACK_SLOTS)
+    uint32_t *fp2 = nullptr;    // combined types: 32-bit occurrence fingerprint per slot, or null
     int32_t *idx = nullptr;     // original index per slot
     uint8_t *len = nullptr;     // length per slot
     uint32_t *row16 = nullptr;  // row byte offset / 16 per slot
@@ -94,6 +95,9 @@ int bucketize(const uint8_t *d_chars, const int64_t *d_off, int64_t n, int64_t t
 void free_bucketed(Bucketed *b, cudaStream_t st);
 // Rebuilds fingerprints of an existing bucketed set from its rows.
 int refingerprint(Bucketed *b, const int8_t *d_map, const FpParams &fp, cudaStream_t st);
+// Combined types: (re)computes b->fp2, the 32-bit occurrence fingerprint of
+// every slot under map2 (allocated on first use), from the rows in slot order.
+int second_fingerprints(Bucketed *b, const int8_t *d_map2, const FpParams &p2, cudaStream_t st);
 // Weight cells.  The W bits of a fingerprint are split into three parts of
 // ceil / floor(W/3) bits (W = 32: bits 21..31, 10..20, 0..9; W = 16: 10..15,
 // 5..9, 0..4); its cell is (x, y, z) = the population counts of the parts,
@@ -261,6 +265,11 @@ struct fp_index {
     int8_t *d_map = nullptr;
     int8_t h_map[256];
     int32_t *d_wstart = nullptr;  // weight order of the buckets (null: position fingerprints, no weight bands)
+    // combined types: a second, 32-bit occurrence fingerprint over the 32 most
+    // frequent symbols (null map: off)
+    int8_t *d_map2 = nullptr;
+    int8_t h_map2[256];
+    fpk::FpParams P2{};
     unsigned long long *d_counts = nullptr;
     int32_t h_count[256];
     int32_t h_start[256];

@@ -117,6 +117,9 @@ struct FilterArgs {
     int idx_bits;
     uint64_t *matches;
     uint64_t match_cap;
+    // combined types: second fingerprints (32-bit occurrence) of the patterns
+    // and the words, or null
+    const uint32_t *qfp2, *dfp2;
 };
 
 // Explicit check of one surviving pair (Sec. 4): Hamming for equal lengths,
@@ -237,9 +240,14 @@ __device__ __forceinline__ void flush_stage(const FilterArgs &A, uint64_t *stage
 // Appends one survivor to the warp's staging buffer.  When it is full the
 // survivor goes to the global list directly, or, in the fused form, is
 // verified on the spot by this thread.
+//
+// With combined types (f3: occurrence + count) a pair that passed the first
+// fingerprint survives only if its second fingerprints pass Eq. 1 as well;
+// each type is sound on its own (Theorem 1), so both must pass for a match.
 template <bool FUSED>
 __device__ __forceinline__ void stage_push(const FilterArgs &A, uint64_t *stage, uint32_t *cnt, uint64_t e, int k,
                                            int metric) {
+    if (A.qfp2 && __popc(A.qfp2[(uint32_t)(e >> 32)] ^ A.dfp2[(uint32_t)e]) > 2 * k) return;
     const uint32_t pos = atomicAdd(cnt, 1u);
     if (pos < FT_STAGE) {
         stage[pos] = e;
@@ -804,6 +812,8 @@ static FilterArgs make_args(const Bucketed &q, const Bucketed &d, const QueryPla
     A.M.high = fp.pos_high | (rep ? fp.pos_high << 16 : 0u);
     A.M.occ = fp.pos_occ | (rep ? fp.pos_occ << 16 : 0u);
     A.tq = cfg.tq < 1 ? 1 : (cfg.tq > FT_MAX_TQ ? FT_MAX_TQ : cfg.tq);
+    A.qfp2 = q.fp2;  // combined types (null otherwise); both sets or neither
+    A.dfp2 = q.fp2 ? d.fp2 : nullptr;
     return A;
 }
 

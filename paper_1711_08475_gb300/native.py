@@ -21,7 +21,7 @@ FP_MODE_TILED, FP_MODE_PLAIN, FP_MODE_FUSED = 0, 1, 2
 
 class fp_build_opts(ctypes.Structure):
     _fields_ = [("set", ctypes.c_int32), ("count_bits", ctypes.c_int32), ("pos_bits", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("custom_map", ctypes.POINTER(ctypes.c_int8))]
+                ("combined", ctypes.c_int32), ("custom_map", ctypes.POINTER(ctypes.c_int8))]
 
 
 class fp_query_opts(ctypes.Structure):

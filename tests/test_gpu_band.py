@@ -214,3 +214,43 @@ def test_batched_plan_falls_back_to_whole_buckets(fp):
             assert np.array_equal(rp[base:base + n + 1] - rp[base], rp0), (tq, n, k, metric)
             assert np.array_equal(idx[rp[base]:rp[base + n]], idx0), (tq, n, k, metric)
             base += n
+
+
+def pair_survivors(d, q, k, metric, fps_d, fps_q):
+    """Eligible pairs whose every fingerprint pair passes Eq. 1 (popc(x) <= 2k)."""
+    ld, lq = d.lengths(), q.lengths()
+    total = 0
+    for i in range(len(q)):
+        sel = (ld == lq[i]) if metric == "ham" else (np.abs(ld.astype(np.int64) - int(lq[i])) <= k)
+        ok = np.ones(int(sel.sum()), dtype=bool)
+        for fd_, fq_ in zip(fps_d, fps_q):
+            ok &= popc(fd_[sel] ^ fq_[i]) <= 2 * k
+        total += int(ok.sum())
+    return total
+
+
+@pytest.mark.parametrize("mode,variant", [("tiled", 0), ("fused", 0), ("tiled", 2), ("plain", 0)])
+def test_combined_types(fp, mode, variant):
+    """Combined types (occurrence + count): a pair survives only if its count32
+    and its occ32 (32 most frequent symbols) fingerprints both pass Eq. 1; the
+    match lists stay the oracle's and the survivors are exactly those pairs."""
+    w = datagen.english1m(20000, 600)
+    d = w.dictionary
+    ix = fp.fp_build(d, fp_type="count", width=32, combined=True)
+    plain = fp.fp_build(d, fp_type="count", width=32)
+    mc = ix.symbol_map()
+    mo, _, _ = oracle.default().symbol_map(d.chars, "common", 32)
+    fd_c = oracle.fingerprints(d, mc, "count", 32).astype(np.uint64)
+    fd_o = oracle.fingerprints(d, mo, "occ", 32).astype(np.uint64)
+    for metric, k in (("ham", 1), ("lev", 1), ("lev", 2)):
+        q = w.queries[metric]
+        r = fp.fp_query_ex(ix, q, k=k, metric=metric, mode=mode, variant=variant)
+        rp0, idx0 = oracle.match(d, q, k, metric)
+        rp, idx = r.csr()
+        assert np.array_equal(rp, rp0) and np.array_equal(idx, idx0), (mode, variant, metric, k)
+        st = r.stats()
+        fq_c = oracle.fingerprints(q, mc, "count", 32).astype(np.uint64)
+        fq_o = oracle.fingerprints(q, mo, "occ", 32).astype(np.uint64)
+        assert st["survivors"] == pair_survivors(d, q, k, metric, (fd_c, fd_o), (fq_c, fq_o))
+        st1 = fp.fp_query_ex(plain, q, k=k, metric=metric, mode=mode, variant=variant).stats()
+        assert st["survivors"] < st1["survivors"] and st["pairs"] == st1["pairs"]
