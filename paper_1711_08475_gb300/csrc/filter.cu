@@ -244,10 +244,10 @@ __device__ __forceinline__ void flush_stage(const FilterArgs &A, uint64_t *stage
 // With combined types (f3: occurrence + count) a pair that passed the first
 // fingerprint survives only if its second fingerprints pass Eq. 1 as well;
 // each type is sound on its own (Theorem 1), so both must pass for a match.
-template <bool FUSED>
+template <bool FUSED, bool COMB>
 __device__ __forceinline__ void stage_push(const FilterArgs &A, uint64_t *stage, uint32_t *cnt, uint64_t e, int k,
                                            int metric) {
-    if (A.qfp2 && __popc(A.qfp2[(uint32_t)(e >> 32)] ^ A.dfp2[(uint32_t)e]) > 2 * k) return;
+    if (COMB && __popc(A.qfp2[(uint32_t)(e >> 32)] ^ A.dfp2[(uint32_t)e]) > 2 * k) return;
     const uint32_t pos = atomicAdd(cnt, 1u);
     if (pos < FT_STAGE) {
         stage[pos] = e;
@@ -361,7 +361,7 @@ __device__ __forceinline__ void make_room(const FilterArgs &A, uint64_t *stage, 
 // count), i.e. (owner lane, tile query), fetches the owner's fingerprints with
 // shuffles and stages every pair of that query and those fingerprints that
 // passes Eq. 1.
-template <int W, int V, bool POS, bool FULL, bool FUSED>
+template <int W, int V, bool POS, bool FULL, bool FUSED, bool COMB>
 __device__ __forceinline__ void retest_round(const FilterArgs &A, const uint32_t *s_q, const uint16_t *queue,
                                              uint32_t first, uint32_t count, uint32_t q0, const uint32_t (&w)[V],
                                              uint32_t invalid, uint32_t T, uint32_t wbase, uint64_t *stage,
@@ -382,7 +382,7 @@ __device__ __forceinline__ void retest_round(const FilterArgs &A, const uint32_t
 #pragma unroll
         for (int i = 0; i < NF; i++)
             if (F[i] <= T && (FULL || !((inv >> i) & 1u)))
-                stage_push<FUSED>(A, stage, cnt, ((uint64_t)(q0 + jq) << 32) | (uint64_t)(wbase + lane_offset<G>(i, src)),
+                stage_push<FUSED, COMB>(A, stage, cnt, ((uint64_t)(q0 + jq) << 32) | (uint64_t)(wbase + lane_offset<G>(i, src)),
                                   k, metric);
     }
 }
@@ -398,7 +398,7 @@ __device__ __forceinline__ void retest_round(const FilterArgs &A, const uint32_t
 // hits), and the warp re-tests the queue in rounds of 32 whenever it holds a
 // full round, so nearly every round keeps all 32 lanes busy; the last partial
 // round runs when the tile ends (the fingerprints in registers belong to it).
-template <int W, int V, bool POS, bool FULL, bool K1MIX, bool FUSED>
+template <int W, int V, bool POS, bool FULL, bool K1MIX, bool FUSED, bool COMB>
 __device__ __forceinline__ void scan_tile(const FilterArgs &A, const uint32_t *s_q, uint32_t nq, uint32_t q0,
                                           const uint32_t (&w)[V], uint32_t invalid, uint32_t T, uint32_t wbase,
                                           uint64_t *stage, uint32_t *cnt, uint16_t *queue, uint32_t *qcnt, int lane,
@@ -435,7 +435,7 @@ __device__ __forceinline__ void scan_tile(const FilterArgs &A, const uint32_t *s
             uint32_t done = 0;
             for (; qn - done >= 32u; done += 32u) {
                 make_room<NF, FUSED>(A, stage, cnt, lane, k, metric);
-                retest_round<W, V, POS, FULL, FUSED>(A, s_q, queue, done, 32u, q0, w, invalid, T, wbase, stage, cnt,
+                retest_round<W, V, POS, FULL, FUSED, COMB>(A, s_q, queue, done, 32u, q0, w, invalid, T, wbase, stage, cnt,
                                                      lane, k, metric);
             }
             if (done) {  // move the rest (< 32) to the front
@@ -460,7 +460,7 @@ __device__ __forceinline__ void scan_tile(const FilterArgs &A, const uint32_t *s
 #pragma unroll
                     for (int i = 0; i < NF; i++)
                         if (F[i] <= T && (FULL || !((invalid >> i) & 1u)))
-                            stage_push<FUSED>(
+                            stage_push<FUSED, COMB>(
                                 A, stage, cnt,
                                 ((uint64_t)(q0 + jb + jj) << 32) | (uint64_t)(wbase + lane_offset<G>(i, lane)), k, metric);
                 }
@@ -476,7 +476,7 @@ __device__ __forceinline__ void scan_tile(const FilterArgs &A, const uint32_t *s
     const uint32_t qn = *qcnt;
     if (qn) {
         make_room<NF, FUSED>(A, stage, cnt, lane, k, metric);
-        retest_round<W, V, POS, FULL, FUSED>(A, s_q, queue, 0u, qn, q0, w, invalid, T, wbase, stage, cnt, lane, k,
+        retest_round<W, V, POS, FULL, FUSED, COMB>(A, s_q, queue, 0u, qn, q0, w, invalid, T, wbase, stage, cnt, lane, k,
                                              metric);
         __syncwarp();
         if (lane == 0) *qcnt = 0;
@@ -490,7 +490,8 @@ constexpr int ft_min_blocks() {
 }
 
 // W: fingerprint width; V: 32-bit words per thread (multiple of 4).
-template <int W, int V, bool POS, bool K1MIX, bool FUSED>
+// COMB: combined types (second fingerprints checked for every pass).
+template <int W, int V, bool POS, bool K1MIX, bool FUSED, bool COMB>
 __global__ void __launch_bounds__(FT_THREADS, (ft_min_blocks<W, V, POS, FUSED>())) k_filter_tiled(FilterArgs A) {
     constexpr int G = (W == 32) ? 4 : 8;             // fingerprints per 128-bit vector
     constexpr int NF = (W == 32) ? V : 2 * V;        // fingerprints per thread
@@ -564,16 +565,16 @@ __global__ void __launch_bounds__(FT_THREADS, (ft_min_blocks<W, V, POS, FUSED>()
             // nothing for this warp in a short tile
         } else if (K1MIX && T != 2u) {  // a k = 1 variant given another k: exact general path
             if (FT_SPLIT_FULL && nw == (uint32_t)TW)
-                scan_tile<W, V, POS, true, false, FUSED>(A, s_q + qa, qn, q0 + qa, w, invalid, T, wbase, stage, cnt, queue, qcnt, lane,
+                scan_tile<W, V, POS, true, false, FUSED, COMB>(A, s_q + qa, qn, q0 + qa, w, invalid, T, wbase, stage, cnt, queue, qcnt, lane,
                                                            S.k, S.metric);
             else
-                scan_tile<W, V, POS, false, false, FUSED>(A, s_q + qa, qn, q0 + qa, w, invalid, T, wbase, stage, cnt, queue, qcnt, lane,
+                scan_tile<W, V, POS, false, false, FUSED, COMB>(A, s_q + qa, qn, q0 + qa, w, invalid, T, wbase, stage, cnt, queue, qcnt, lane,
                                                            S.k, S.metric);
         } else if (FT_SPLIT_FULL && nw == (uint32_t)TW) {
-            scan_tile<W, V, POS, true, K1MIX, FUSED>(A, s_q + qa, qn, q0 + qa, w, invalid, T, wbase, stage, cnt, queue, qcnt, lane,
+            scan_tile<W, V, POS, true, K1MIX, FUSED, COMB>(A, s_q + qa, qn, q0 + qa, w, invalid, T, wbase, stage, cnt, queue, qcnt, lane,
                                                            S.k, S.metric);
         } else {
-            scan_tile<W, V, POS, false, K1MIX, FUSED>(A, s_q + qa, qn, q0 + qa, w, invalid, T, wbase, stage, cnt, queue, qcnt, lane,
+            scan_tile<W, V, POS, false, K1MIX, FUSED, COMB>(A, s_q + qa, qn, q0 + qa, w, invalid, T, wbase, stage, cnt, queue, qcnt, lane,
                                                            S.k, S.metric);
         }
         // fused: the next tile may have another (k, metric), so verify what is staged
@@ -619,7 +620,7 @@ __device__ __forceinline__ void mma_e4m3_f16(uint32_t &d0, uint32_t &d1, const u
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "r"(c));
 }
 
-template <int W, bool FUSED>
+template <int W, bool FUSED, bool COMB>
 __global__ void __launch_bounds__(FM_THREADS, FM_MIN_BLOCKS) k_filter_mma(FilterArgs A) {
     __shared__ uint2 s_lut[256];  // byte -> eight E4M3 values (+1 for a set bit, -1 for a clear one)
     __shared__ uint32_t s_q[FM_TQ];
@@ -716,7 +717,7 @@ __global__ void __launch_bounds__(FM_THREADS, FM_MIN_BLOCKS) k_filter_mma(Filter
                         const uint32_t row = (uint32_t)(r * 16 + g + (h >> 1) * 8);
                         const uint32_t col = wrel + 2u * (uint32_t)t + (uint32_t)(h & 1);
                         if (row < nq && col < nw)
-                            stage_push<FUSED>(A, stage, cnt, ((uint64_t)(q0 + row) << 32) | (uint64_t)(w0 + col), S.k,
+                            stage_push<FUSED, COMB>(A, stage, cnt, ((uint64_t)(q0 + row) << 32) | (uint64_t)(w0 + col), S.k,
                                               S.metric);
                     }
                 }
@@ -733,35 +734,35 @@ __global__ void __launch_bounds__(FM_THREADS, FM_MIN_BLOCKS) k_filter_mma(Filter
     if (!FUSED) flush_stage(A, stage, cnt, lane);
 }
 
-template <int W, bool FUSED>
+template <int W, bool FUSED, bool COMB>
 static int launch_mma(const FilterArgs &A, cudaStream_t st) {
     static int grid = 0;
     if (grid == 0) {
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_mma<W, FUSED>, FM_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_mma<W, FUSED, COMB>, FM_THREADS, 0);
         grid = sm_count() * (per_sm > 0 ? per_sm : 1);
     }
-    k_filter_mma<W, FUSED><<<grid, FM_THREADS, 0, st>>>(A);
+    k_filter_mma<W, FUSED, COMB><<<grid, FM_THREADS, 0, st>>>(A);
     FP_LAUNCHED(FUSED ? "k_filter_mma(fused)" : "k_filter_mma");
     return FP_OK;
 }
 
-template <int W, int V, bool POS, bool FUSED>
+template <int W, int V, bool POS, bool FUSED, bool COMB = false>
 static int launch_one(const FilterArgs &A, bool k1mix, cudaStream_t st) {
     static int grid[2] = {0, 0};
     int &g = grid[k1mix ? 1 : 0];
     if (g == 0) {
         int per_sm = 0;
         if (k1mix)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_tiled<W, V, POS, (W == 32 && !POS), FUSED>,
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_tiled<W, V, POS, (W == 32 && !POS), FUSED, COMB>,
                                                           FT_THREADS, 0);
         else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_tiled<W, V, POS, false, FUSED>, FT_THREADS,
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_tiled<W, V, POS, false, FUSED, COMB>, FT_THREADS,
                                                           0);
         g = sm_count() * (per_sm > 0 ? per_sm : 1);
     }
-    if (k1mix) k_filter_tiled<W, V, POS, (W == 32 && !POS), FUSED><<<g, FT_THREADS, 0, st>>>(A);
-    else k_filter_tiled<W, V, POS, false, FUSED><<<g, FT_THREADS, 0, st>>>(A);
+    if (k1mix) k_filter_tiled<W, V, POS, (W == 32 && !POS), FUSED, COMB><<<g, FT_THREADS, 0, st>>>(A);
+    else k_filter_tiled<W, V, POS, false, FUSED, COMB><<<g, FT_THREADS, 0, st>>>(A);
     FP_LAUNCHED(FUSED ? "k_filter_tiled(fused)" : "k_filter_tiled");
     return FP_OK;
 }
@@ -769,7 +770,15 @@ static int launch_one(const FilterArgs &A, bool k1mix, cudaStream_t st) {
 template <bool FUSED>
 static int dispatch(const FilterArgs &A, const FpParams &fp, const FilterCfg &cfg, cudaStream_t st) {
     const bool pos = fp.type == FP_POS;
-    if (cfg.mma && !pos) return fp.width == 32 ? launch_mma<32, FUSED>(A, st) : launch_mma<16, FUSED>(A, st);
+    // combined types (32-bit count fingerprints only): their own instances, so
+    // that the other kernels carry no second check
+    const bool comb = A.qfp2 != nullptr && fp.width == 32 && !pos;
+    const bool mix0 = cfg.k1mix && fp.width == 32 && !pos;
+    if (comb) {
+        if (cfg.mma) return launch_mma<32, FUSED, true>(A, st);
+        return launch_one<32, 4, false, FUSED, true>(A, mix0, st);
+    }
+    if (cfg.mma && !pos) return fp.width == 32 ? launch_mma<32, FUSED, false>(A, st) : launch_mma<16, FUSED, false>(A, st);
     // the mixed POPC / ALU test applies to 32-bit popcount-type fingerprints at k = 1
     const bool mix = cfg.k1mix && fp.width == 32 && !pos;
     if (FUSED) {  // the fused form is built for 4 words per thread only
