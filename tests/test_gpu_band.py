@@ -14,6 +14,7 @@ import pytest
 
 import datagen
 import oracle
+from band_rule import expected_tested, popc
 
 pytestmark = pytest.mark.gpu
 
@@ -28,78 +29,6 @@ def fp():
     build.build()
     import paper_1711_08475_gb300 as m
     return m
-
-
-def popc(x):
-    x = np.asarray(x, dtype=np.uint64)
-    return np.array([bin(int(v)).count("1") for v in x], dtype=np.int64)
-
-
-def part_bits(width):
-    """Bits of the three parts, most significant part first (W = 32: 11, 11, 10)."""
-    return [width // 3 + (1 if i < width % 3 else 0) for i in range(3)]
-
-
-def cells(f, width):
-    b0, b1, b2 = part_bits(width)
-    f = np.asarray(f, dtype=np.uint64)
-    x = popc(f >> np.uint64(b1 + b2))
-    y = popc((f >> np.uint64(b2)) & np.uint64((1 << b1) - 1))
-    z = popc(f & np.uint64((1 << b2) - 1))
-    return (x * (b1 + 1) + y) * (b2 + 1) + z
-
-
-def expected_tested(d, q, k, metric, m, t, width, tq):
-    """Pairs a banded plan tests.  Per length bin the patterns sorted by cell
-    are cut into tiles of tq.  With (x1, y1, z1), (x2, y2, z2) the cells of a
-    tile's first and last pattern, its box is x in [x1, x2], y in [y1, y2] if
-    x1 = x2 (else everything), z in [z1, z2] if also y1 = y2 (else
-    everything).  In every dictionary bucket of an admissible length, for
-    every (x', y') whose L1 distance to the box's x and y ranges is at most
-    2k, the tile tests the words of cells (x', y', z') with z' within the
-    remaining distance of the z range: one run of slots, started at the
-    bucket's 8-slot boundary below its first word; runs that then touch or
-    overlap are merged."""
-    b0, b1, b2 = part_bits(width)
-    R1, R2 = b1 + 1, b2 + 1
-    cq = cells(oracle.fingerprints(q, m, t, width), width)
-    cd = cells(oracle.fingerprints(d, m, t, width), width)
-    lq, ld = q.lengths(), d.lengths()
-    by_len = {L: np.sort(cd[ld == L]) for L in np.unique(ld)}
-    dist = lambda v, lo, hi: max(lo - v, 0, v - hi)
-    total = 0
-    for n in np.unique(lq):
-        cs = np.sort(cq[lq == n])
-        lens = [n] if metric == "ham" else range(max(0, n - k), min(255, n + k) + 1)
-        for s in range(0, len(cs), tq):
-            tile = cs[s:s + tq]
-            f, l = int(tile[0]), int(tile[-1])
-            xa, xb = f // (R1 * R2), l // (R1 * R2)
-            y1, y2, z1, z2 = f // R2 % R1, l // R2 % R1, f % R2, l % R2
-            ya, yb = (y1, y2) if xa == xb else (0, b1)
-            za, zb = (z1, z2) if xa == xb and y1 == y2 else (0, b2)
-            for L in lens:
-                if L not in by_len:
-                    continue
-                b = by_len[L]
-                runs = []
-                for x in range(max(0, xa - 2 * k), min(b0, xb + 2 * k) + 1):
-                    r1 = 2 * k - dist(x, xa, xb)
-                    for y in range(max(0, ya - r1), min(b1, yb + r1) + 1):
-                        r2 = r1 - dist(y, ya, yb)
-                        zlo, zhi = max(0, za - r2), min(b2, zb + r2)
-                        c = (x * R1 + y) * R2
-                        first = int(np.searchsorted(b, c + zlo, side="left"))
-                        end = int(np.searchsorted(b, c + zhi + 1, side="left"))
-                        if end <= first:
-                            continue
-                        s8 = first & ~7
-                        if runs and s8 <= runs[-1][1]:
-                            runs[-1][1] = max(runs[-1][1], end)
-                        else:
-                            runs.append([s8, end])
-                total += len(tile) * sum(e - a for a, e in runs)
-    return total
 
 
 @pytest.mark.parametrize("t,width", [("occ", 32), ("count", 32), ("occ", 16), ("occh", 16)])
