@@ -24,6 +24,7 @@ HAM, LEV = 0, 1
 OCC, OCCH, COUNT, POS = 0, 1, 2, 3
 TYPES = {"occ": OCC, "occh": OCCH, "count": COUNT, "pos": POS}
 METRICS = {"ham": HAM, "lev": LEV}
+FD_KINDS = {"weight": 0, "count_l1": 1}  # distance of orc_filter_match_fps / orc_bound_violations_fps
 SET_COMMON, SET_RARE, SET_MIXED = 0, 1, 2
 SETS = {"common": SET_COMMON, "rare": SET_RARE, "mixed": SET_MIXED}
 
@@ -71,6 +72,19 @@ def _bind(path: str):
     L.orc_filter_match.restype = i32
     L.orc_bound_violations.argtypes = [u8p, i64p, i64, i8p, i32, i32, i32, i32, i32, i32, i64p]
     L.orc_bound_violations.restype = None
+    L.orc_fd_count_l1.argtypes = [ctypes.c_uint32, ctypes.c_uint32, i32, i32]
+    L.orc_fd_count_l1.restype = i32
+    L.orc_qgram_map.argtypes = [u8p, i64p, i64, i32, i32, u8p, i64p]
+    L.orc_qgram_map.restype = i32
+    L.orc_fp_qgram.argtypes = [u8p, i64, u8p, i32, i32]
+    L.orc_fp_qgram.restype = ctypes.c_uint32
+    L.orc_fp_qgram_many.argtypes = [u8p, i64p, i64, u8p, i32, i32, u32p]
+    L.orc_fp_qgram_many.restype = None
+    L.orc_filter_match_fps.argtypes = [u8p, i64p, i64, u8p, i64p, i64, i32, i32, u32p, u32p, i32, i32, i32,
+                                       i32, i32, i64p, ctypes.POINTER(i32p), i64p]
+    L.orc_filter_match_fps.restype = i32
+    L.orc_bound_violations_fps.argtypes = [u8p, i64p, i64, u32p, i32, i32, i32, i32, i32, i64p]
+    L.orc_bound_violations_fps.restype = None
     L.orc_free.argtypes = [ctypes.c_void_p]
     L.orc_free.restype = None
     return L
@@ -193,6 +207,34 @@ class Oracle:
         lay = layout(type_name, width, 2, p)
         return int(self.L.orc_fd(a, b, TYPES[type_name], width, p, lay["n_pos"]))
 
+    def fd_count_l1(self, a: int, b: int, width: int, bits: int = 2) -> int:
+        """Sum over count fields of |c1 - c2| (binary-coded counts, Sec. 3.3 remark)."""
+        return int(self.L.orc_fd_count_l1(a, b, width, bits))
+
+    def qgram_map(self, strings, q: int, sigma: int = 32):
+        """(grams uint8[used, q], counts int64[used]): the sigma most frequent q-grams."""
+        g = np.zeros(max(sigma * q, 1), dtype=np.uint8)
+        c = np.zeros(max(sigma, 1), dtype=np.int64)
+        used = self.L.orc_qgram_map(_p(_nz(strings.chars), ctypes.c_uint8), _p(strings.offsets, ctypes.c_int64),
+                                    len(strings), q, sigma, _p(g, ctypes.c_uint8), _p(c, ctypes.c_int64))
+        if used < 0:
+            raise ValueError("q must be 1..3")
+        return g[:used * q].reshape(used, q), c[:used]
+
+    def qgram_fingerprint(self, s, grams: np.ndarray) -> int:
+        S = _bytes(s)
+        g = np.ascontiguousarray(grams, dtype=np.uint8)
+        return int(self.L.orc_fp_qgram(_p(S, ctypes.c_uint8), len(s), _p(_nz(g.reshape(-1)), ctypes.c_uint8),
+                                       g.shape[0], g.shape[1] if g.ndim == 2 else 1))
+
+    def qgram_fingerprints(self, strings, grams: np.ndarray) -> np.ndarray:
+        g = np.ascontiguousarray(grams, dtype=np.uint8)
+        out = np.zeros(max(len(strings), 1), dtype=np.uint32)
+        self.L.orc_fp_qgram_many(_p(_nz(strings.chars), ctypes.c_uint8), _p(strings.offsets, ctypes.c_int64),
+                                 len(strings), _p(_nz(g.reshape(-1)), ctypes.c_uint8), g.shape[0], g.shape[1],
+                                 _p(out, ctypes.c_uint32))
+        return out[:len(strings)]
+
     # -- matchers ----------------------------------------------------------
     def _collect(self, rc, row_ptr, idx_p):
         if rc != 0:
@@ -230,6 +272,34 @@ class Oracle:
                                      _p(stats, ctypes.c_int64))
         rp, idx = self._collect(rc, row_ptr, idx_p)
         return rp, idx, int(stats[0]), int(stats[1])
+
+    def filter_match_fps(self, dictionary, queries, k: int, metric: str, dfp: np.ndarray, qfp: np.ndarray,
+                         kind: str = "weight", width: int = 32, bits: int = 2, q: int = 1, threads: int = 0):
+        """The Sec. 4 method on given fingerprints, bound D >= ceil(F_D / 2q): (row_ptr, idx, pairs, survivors)."""
+        d, qs = dictionary, queries
+        row_ptr = np.zeros(len(qs) + 1, dtype=np.int64)
+        stats = np.zeros(2, dtype=np.int64)
+        idx_p = ctypes.POINTER(ctypes.c_int32)()
+        df = np.ascontiguousarray(_nz(np.asarray(dfp, dtype=np.uint32)))
+        qf = np.ascontiguousarray(_nz(np.asarray(qfp, dtype=np.uint32)))
+        rc = self.L.orc_filter_match_fps(_p(_nz(d.chars), ctypes.c_uint8), _p(d.offsets, ctypes.c_int64), len(d),
+                                         _p(_nz(qs.chars), ctypes.c_uint8), _p(qs.offsets, ctypes.c_int64), len(qs),
+                                         k, METRICS[metric], _p(df, ctypes.c_uint32), _p(qf, ctypes.c_uint32),
+                                         FD_KINDS[kind], width, bits, q, threads, _p(row_ptr, ctypes.c_int64),
+                                         ctypes.byref(idx_p), _p(stats, ctypes.c_int64))
+        rp, idx = self._collect(rc, row_ptr, idx_p)
+        return rp, idx, int(stats[0]), int(stats[1])
+
+    def bound_violations_fps(self, strings, fp: np.ndarray, kind: str, width: int, metric: str, bits: int = 2,
+                             q: int = 1) -> dict:
+        """Exhaustive check of D >= ceil(F_D / 2q) over all pairs of strings with lengths within 1."""
+        out = np.zeros(4, dtype=np.int64)
+        f = np.ascontiguousarray(_nz(np.asarray(fp, dtype=np.uint32)))
+        self.L.orc_bound_violations_fps(_p(_nz(strings.chars), ctypes.c_uint8), _p(strings.offsets, ctypes.c_int64),
+                                        len(strings), _p(f, ctypes.c_uint32), FD_KINDS[kind], width, bits, q,
+                                        METRICS[metric], _p(out, ctypes.c_int64))
+        return {"pairs": int(out[0]), "violations": int(out[1]),
+                "example": (int(out[2]), int(out[3])) if out[1] else None}
 
     def bound_violations(self, strings, map_: np.ndarray, type_name: str, width: int, metric: str,
                          b: int = 2, p: int = 3, gray: bool = True) -> dict:
@@ -302,3 +372,23 @@ def filter_match(dictionary, queries, k, metric, map_, type_name, width, b=2, p=
 
 def bound_violations(strings, map_, type_name, width, metric, b=2, p=3, gray=True):
     return default().bound_violations(strings, map_, type_name, width, metric, b, p, gray)
+
+
+def fd_count_l1(a, b, width, bits=2):
+    return default().fd_count_l1(a, b, width, bits)
+
+
+def qgram_map(strings, q, sigma=32):
+    return default().qgram_map(strings, q, sigma)
+
+
+def qgram_fingerprints(strings, grams):
+    return default().qgram_fingerprints(strings, grams)
+
+
+def filter_match_fps(dictionary, queries, k, metric, dfp, qfp, kind="weight", width=32, bits=2, q=1, threads=0):
+    return default().filter_match_fps(dictionary, queries, k, metric, dfp, qfp, kind, width, bits, q, threads)
+
+
+def bound_violations_fps(strings, fp, kind, width, metric, bits=2, q=1):
+    return default().bound_violations_fps(strings, fp, kind, width, metric, bits, q)

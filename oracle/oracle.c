@@ -32,6 +32,22 @@
  *                          of the XOR of the trailing occurrence bits.
  *   orc_symbol_map         Common / rare / mixed symbol sets, Sec. 3, chosen
  *                          by occurrence counts over the collection.
+ *   orc_fd_count_l1        Count fingerprints compared field by field: the sum
+ *                          over fields of |c1 - c2| of the saturating counts in
+ *                          the paper's binary code (the remark after Eq. 1 in
+ *                          Sec. 3.3 that the Hamming weight under-counts count
+ *                          differences: 3 (11) against 1 (01) differ by 2).
+ *   orc_qgram_map          q-gram fingerprints (the future work of Sec. 5: the
+ *   orc_fp_qgram           fingerprint of Sec. 3.2 over q-grams instead of
+ *                          single symbols): the sigma most frequent q-grams of
+ *                          the collection each own a bit, set iff the q-gram
+ *                          occurs in the string.  One edit touches at most q
+ *                          q-grams on each side, so F_D grows by at most 2q
+ *                          per edit and D >= ceil(F_D / 2q) (the argument of
+ *                          Theorem 1 with 2q in place of 2).
+ *   orc_filter_match_fps   The Sec. 4 method on given fingerprints and a given
+ *   orc_bound_violations_fps  distance (Hamming weight, or the count L1), with
+ *                          the bound D >= ceil(F_D / 2q) (q = 1: Eq. 1).
  *   orc_filter_match       The paper's own method, Sec. 4: the query
  *                          fingerprint is built once, each eligible word is
  *                          rejected when ceil(F_D/2) > k (Eq. 1), otherwise it
@@ -242,6 +258,96 @@ int orc_fd(uint32_t a, uint32_t b, int type, int width, int p, int n_pos)
     return f + (top < 32 ? weight(x >> top) : 0);
 }
 
+/* Count fingerprints in the paper's binary code (Sec. 3.2), compared by the
+ * distance of the counts themselves: field q (bits [bits*q, bits*q + bits)
+ * below width) holds a saturating count; the result is the sum over fields of
+ * |count1 - count2|.  A substitution moves one count down and one up by at
+ * most one each, an insertion or deletion one count by at most one, so this
+ * sum grows by at most 2 per edit and Eq. 1 holds for it. */
+int orc_fd_count_l1(uint32_t a, uint32_t b, int width, int bits)
+{
+    uint32_t fmask = ((uint32_t)1 << bits) - 1;
+    int f = 0;
+    for (int q = 0; (q + 1) * bits <= width; q++) {
+        int ca = (int)((a >> (bits * q)) & fmask);
+        int cb = (int)((b >> (bits * q)) & fmask);
+        f += ca > cb ? ca - cb : cb - ca;
+    }
+    return f;
+}
+
+/* ------------------------------------------------------------------------ */
+/* q-gram fingerprints (Sec. 5, future work)                                */
+/* ------------------------------------------------------------------------ */
+
+static uint32_t gram_code(const uint8_t *s, int q)
+{
+    uint32_t c = 0;
+    for (int j = 0; j < q; j++)
+        c = (c << 8) | s[j];
+    return c;
+}
+
+/* The sigma most frequent q-grams (1 <= q <= 3) over all positions of all
+ * strings, most frequent first, ties broken by the smaller q-gram in byte
+ * order (the code with the first byte most significant); only q-grams that
+ * occur are eligible.  Field f is the f-th q-gram: its q bytes are written to
+ * grams_out[f*q .. f*q+q) and its count to counts_out[f] (if given).
+ * Returns the number of fields used, or -1 (bad q, or no memory). */
+int orc_qgram_map(const uint8_t *chars, const int64_t *off, int64_t n_str, int q, int sigma,
+                  uint8_t *grams_out, int64_t *counts_out)
+{
+    if (q < 1 || q > 3 || sigma < 0)
+        return -1;
+    size_t ncodes = (size_t)1 << (8 * q);
+    int64_t *cnt = (int64_t *)calloc(ncodes, sizeof(int64_t));
+    if (!cnt)
+        return -1;
+    for (int64_t i = 0; i < n_str; i++) {
+        int64_t n = off[i + 1] - off[i];
+        for (int64_t j = 0; j + q <= n; j++)
+            cnt[gram_code(chars + off[i] + j, q)]++;
+    }
+    int used = 0;
+    while (used < sigma) {
+        size_t best = 0;
+        int64_t bc = 0;
+        for (size_t c = 0; c < ncodes; c++)
+            if (cnt[c] > bc) { /* strict: the first (smallest) code wins a tie */
+                bc = cnt[c];
+                best = c;
+            }
+        if (bc == 0)
+            break;
+        for (int j = 0; j < q; j++)
+            grams_out[used * q + j] = (uint8_t)(best >> (8 * (q - 1 - j)));
+        if (counts_out)
+            counts_out[used] = bc;
+        cnt[best] = 0; /* taken */
+        used++;
+    }
+    free(cnt);
+    return used;
+}
+
+/* Bit f is set iff the f-th q-gram of the map occurs somewhere in s. */
+uint32_t orc_fp_qgram(const uint8_t *s, int64_t n, const uint8_t *grams, int n_grams, int q)
+{
+    uint32_t fp = 0;
+    for (int64_t i = 0; i + q <= n; i++)
+        for (int f = 0; f < n_grams && f < 32; f++)
+            if (memcmp(s + i, grams + (size_t)f * q, (size_t)q) == 0)
+                fp |= (uint32_t)1 << f;
+    return fp;
+}
+
+void orc_fp_qgram_many(const uint8_t *chars, const int64_t *off, int64_t n_str, const uint8_t *grams,
+                       int n_grams, int q, uint32_t *out)
+{
+    for (int64_t i = 0; i < n_str; i++)
+        out[i] = orc_fp_qgram(chars + off[i], off[i + 1] - off[i], grams, n_grams, q);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Symbol sets (Sec. 3): common, rare, mixed                                */
 /* ------------------------------------------------------------------------ */
@@ -391,6 +497,16 @@ int orc_lev_within(const uint8_t *a, int64_t n, const uint8_t *b, int64_t m, int
 /* Matchers: brute force, and the paper's filter + verify                    */
 /* ------------------------------------------------------------------------ */
 
+#define ORC_FD_WEIGHT 0   /* Hamming weight of the XOR (occurrence, q-gram) */
+#define ORC_FD_COUNT_L1 1 /* orc_fd_count_l1 */
+
+static int fd_given(uint32_t a, uint32_t b, int kind, int width, int bits)
+{
+    if (kind == ORC_FD_COUNT_L1)
+        return orc_fd_count_l1(a, b, width, bits);
+    return orc_fd(a, b, ORC_OCC, width, 0, 0);
+}
+
 typedef struct {
     int32_t *v;
     int64_t n, cap;
@@ -421,6 +537,7 @@ typedef struct {
     int k, metric, prune;
     /* filter mode */
     int use_filter, type, width, p, n_pos;
+    int fd_kind, bits, qmul; /* given-fingerprint mode: distance kind, count bits, bound 2*qmul*k */
     const uint32_t *dfp;
     const uint32_t *qfp;
     /* outputs */
@@ -445,9 +562,16 @@ static void run_query(job_t *J, int64_t q, int64_t *pairs, int64_t *surv, int64_
             if (J->metric == ORC_HAM ? (m != n) : (m - n > J->k || n - m > J->k))
                 continue;
             (*pairs)++;
-            int f = orc_fd(J->qfp[q], J->dfp[i], J->type, J->width, J->p, J->n_pos);
-            if ((f + 1) / 2 > J->k) /* Eq. 1: D >= ceil(F_D / 2) */
-                continue;
+            if (J->use_filter == 1) {
+                int f = orc_fd(J->qfp[q], J->dfp[i], J->type, J->width, J->p, J->n_pos);
+                if ((f + 1) / 2 > J->k) /* Eq. 1: D >= ceil(F_D / 2) */
+                    continue;
+            } else {
+                int f = fd_given(J->qfp[q], J->dfp[i], J->fd_kind, J->width, J->bits);
+                int div = 2 * J->qmul;
+                if ((f + div - 1) / div > J->k) /* D >= ceil(F_D / 2q) */
+                    continue;
+            }
             (*surv)++;
             hit = J->metric == ORC_HAM ? orc_ham_within(P, n, S, m, J->k)
                                        : orc_lev_within(P, n, S, m, J->k);
@@ -593,6 +717,39 @@ int orc_filter_match(const uint8_t *dchars, const int64_t *doff, int64_t nd, con
     return rc;
 }
 
+/* The Sec. 4 method on fingerprints computed by the caller: a pair is
+ * rejected when ceil(F_D / 2q) > k, F_D of the given kind, otherwise
+ * verified as in orc_filter_match.  q = 1 is Eq. 1. */
+int orc_filter_match_fps(const uint8_t *dchars, const int64_t *doff, int64_t nd, const uint8_t *qchars,
+                         const int64_t *qoff, int64_t nq, int k, int metric, const uint32_t *dfp,
+                         const uint32_t *qfp, int fd_kind, int width, int bits, int q, int nthreads,
+                         int64_t *row_ptr, int32_t **idx_out, int64_t *stats)
+{
+    job_t J;
+    memset(&J, 0, sizeof J);
+    J.dchars = dchars;
+    J.doff = doff;
+    J.nd = nd;
+    J.qchars = qchars;
+    J.qoff = qoff;
+    J.nq = nq;
+    J.k = k;
+    J.metric = metric;
+    J.use_filter = 2;
+    J.fd_kind = fd_kind;
+    J.width = width;
+    J.bits = bits;
+    J.qmul = q;
+    J.dfp = dfp;
+    J.qfp = qfp;
+    int rc = run_job(&J, nthreads, row_ptr, idx_out);
+    if (stats) {
+        stats[0] = J.pairs;
+        stats[1] = J.survivors;
+    }
+    return rc;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Exhaustive check of Eq. 1 (Theorems 1 and 2) over a set of strings        */
 /* ------------------------------------------------------------------------ */
@@ -635,6 +792,38 @@ void orc_bound_violations(const uint8_t *chars, const int64_t *off, int64_t n_st
         }
     }
     free(fp);
+}
+
+/* The same check on fingerprints computed by the caller, for the bound
+ * D >= ceil(F_D / 2q) with F_D of the given kind (q = 1: Eq. 1). */
+void orc_bound_violations_fps(const uint8_t *chars, const int64_t *off, int64_t n_str, const uint32_t *fp,
+                              int fd_kind, int width, int bits, int q, int metric, int64_t *out)
+{
+    out[0] = out[1] = 0;
+    out[2] = out[3] = -1;
+    int div = 2 * q;
+    for (int64_t i = 0; i < n_str; i++) {
+        const uint8_t *s = chars + off[i];
+        int64_t n = off[i + 1] - off[i];
+        for (int64_t j = 0; j < n_str; j++) {
+            const uint8_t *t = chars + off[j];
+            int64_t m = off[j + 1] - off[j];
+            if (m - n > 1 || n - m > 1)
+                continue;
+            int64_t d = metric == ORC_HAM ? orc_ham(s, n, t, m) : orc_lev(s, n, t, m);
+            if (d < 0)
+                continue;
+            out[0]++;
+            int f = fd_given(fp[i], fp[j], fd_kind, width, bits);
+            if (d < (f + div - 1) / div) {
+                if (out[1] == 0) {
+                    out[2] = i;
+                    out[3] = j;
+                }
+                out[1]++;
+            }
+        }
+    }
 }
 
 void orc_free(void *p) { free(p); }

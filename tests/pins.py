@@ -430,10 +430,151 @@ def check_filter_decision(orc):
     assert (pairs, surv) == (3, 3)
 
 
+# ---------------------------------------------------------------------------
+# Count fingerprints compared by the L1 distance of the counts (Sec. 3.3)
+# ---------------------------------------------------------------------------
+
+
+def _unary(fields, bits):
+    """Thermometer code of saturating counts: value v of a field as v ones in
+    2^bits - 1 bit positions (popc of the XOR of two codes = |v1 - v2|)."""
+    width = (1 << bits) - 1
+    u = 0
+    for i, v in enumerate(fields):
+        u |= ((1 << v) - 1) << (width * i)
+    return u
+
+
+def _pack(fields, bits):
+    return sum(v << (bits * i) for i, v in enumerate(fields))
+
+
+def check_count_l1(orc):
+    # the remark after Eq. 1: a count of 3 (11) against a count of 1 (01)
+    # differs by 2, where the Hamming weight of the XOR gives 1
+    assert orc.fd_count_l1(0b11, 0b01, 2, 2) == 2
+    assert orc.fd(0b11, 0b01, "count", 2) == 1
+    # hand values over several fields (field 0 in the low bits)
+    assert orc.fd_count_l1(_pack([0, 3, 1, 2], 2), _pack([3, 0, 2, 1], 2), 8, 2) == 8
+    assert orc.fd_count_l1(_pack([7, 0, 5], 3), _pack([0, 7, 5], 3), 9, 3) == 14
+    assert orc.fd_count_l1(_pack([1] * 16, 2), _pack([1] * 16, 2), 32, 2) == 0
+    # fields above the width do not count
+    assert orc.fd_count_l1(0b1100, 0, 2, 2) == 0
+    # from strings: aaab -> counts (3, 1), ab -> (1, 1) in the binary code
+    m = map_from_order(b"ab")
+    fa = orc.fingerprint(b"aaab", m, "count", 16, gray=False)
+    fb = orc.fingerprint(b"ab", m, "count", 16, gray=False)
+    assert orc.fd_count_l1(fa, fb, 16, 2) == 2 and orc.lev(b"aaab", b"ab") == 2
+    # against the thermometer code on random count vectors (a different
+    # computation of the same distance), and never below the Gray-code
+    # distance, equal to it unless some field differs by 3
+    r = datagen.randint(datagen.stream_key(3, "l1"), 2 * 16 * 300, 0, 3).reshape(300, 2, 16)
+    for a, b in r:
+        la = orc.fd_count_l1(_pack(a, 2), _pack(b, 2), 32, 2)
+        assert la == bin(_unary(a, 2) ^ _unary(b, 2)).count("1")
+        ga = _pack([v ^ (v >> 1) for v in a], 2)
+        gb = _pack([v ^ (v >> 1) for v in b], 2)
+        gray = bin(ga ^ gb).count("1")
+        assert la >= gray
+        assert (la == gray) == (not np.any(np.abs(a.astype(int) - b.astype(int)) == 3))
+
+
+def check_count_l1_sweep(orc, max_len: int = 5, n_random_maps: int = 3, seed: int = 5):
+    """Eq. 1 with the L1 count distance on the paper's binary code: zero
+    violations (b = 1, 2, 3), where the Hamming weight of the same binary
+    fingerprints has violations (check_bound_sweep)."""
+    S = datagen.Strings.from_list(all_strings(SWEEP_ALPHABET, max_len))
+    small = datagen.Strings.from_list(all_strings(SWEEP_ALPHABET, min(max_len, 4)))
+    for metric in ("ham", "lev"):
+        for b, width in ((2, 8), (3, 9), (1, 8)):
+            sigma = width // b
+            maps = [map_from_order(SWEEP_ALPHABET[:sigma]), map_from_order(SWEEP_ALPHABET[:3][:sigma])]
+            runs = [(S, m) for m in maps] + [(small, m) for m in random_maps(seed, n_random_maps, SWEEP_ALPHABET,
+                                                                              sigma)]
+            for strs, m in runs:
+                fp = orc.fingerprints(strs, m, "count", width, b=b, gray=False)
+                r = orc.bound_violations_fps(strs, fp, "count_l1", width, metric, bits=b)
+                assert r["pairs"] > 0 and r["violations"] == 0, (metric, b, r)
+
+
+# ---------------------------------------------------------------------------
+# q-gram fingerprints (Sec. 5): occurrence of the most frequent q-grams
+# ---------------------------------------------------------------------------
+
+
+def check_qgram_fingerprints(orc):
+    S = datagen.Strings.from_list([b"abab", b"abc"])
+    grams, counts = orc.qgram_map(S, 2, 32)
+    # bigram occurrences: ab 3 (abab twice, abc once), ba 1, bc 1; ba before bc
+    assert [bytes(g) for g in grams] == [b"ab", b"ba", b"bc"] and list(counts) == [3, 1, 1]
+    fps = [orc.qgram_fingerprint(s, grams) for s in (b"abab", b"abc", b"cab", b"bcab", b"b", b"")]
+    assert fps == [0b011, 0b101, 0b001, 0b101, 0, 0], fps
+    # ties go to the smaller q-gram in byte order, whatever the order of appearance
+    g2, _ = orc.qgram_map(datagen.Strings.from_list([b"ba", b"ab"]), 2, 32)
+    assert [bytes(g) for g in g2] == [b"ab", b"ba"]
+    # sigma caps the fields; trigrams
+    g3, c3 = orc.qgram_map(datagen.Strings.from_list([b"abcd", b"xbcd"]), 3, 2)
+    assert [bytes(g) for g in g3] == [b"bcd", b"abc"] and list(c3) == [2, 1]
+    assert orc.qgram_fingerprint(b"abcd", g3) == 0b11 and orc.qgram_fingerprint(b"abc", g3) == 0b10
+    # q = 1 is the occurrence fingerprint over the common symbols (Sec. 3.2)
+    w = datagen.english1m(2000, 10)
+    g1, _ = orc.qgram_map(w.dictionary, 1, 16)
+    m, _, _ = orc.symbol_map(w.dictionary.chars, "common", 16)
+    assert all(m[g[0]] == f for f, g in enumerate(g1)) and (m >= 0).sum() == len(g1)
+    assert np.array_equal(orc.qgram_fingerprints(w.dictionary, g1), orc.fingerprints(w.dictionary, m, "occ", 16))
+
+
+def check_qgram_sweep(orc, max_len: int = 5, seed: int = 9):
+    """One edit changes the q-gram fingerprint by at most 2q bits, so
+    D >= ceil(F_D / 2q): zero violations over every string of length <= 5 on
+    {a, b, c, x} (q = 2, 3; the collection's own q-grams and random sets);
+    the Eq. 1 bound (2 in place of 2q) has violations, so the sweep bites."""
+    S = datagen.Strings.from_list(all_strings(SWEEP_ALPHABET, max_len))
+    for q in (2, 3):
+        sets = [orc.qgram_map(S, q, 12)[0]]
+        every = list(itertools.product(SWEEP_ALPHABET, repeat=q))
+        for t in range(2):  # random sets of 12 distinct q-grams (each q-gram owns at most one bit)
+            pick = datagen.permutation(datagen.stream_key(seed, f"grams{q}/{t}"), len(every))[:12]
+            sets.append(np.array([every[i] for i in pick], dtype=np.uint8))
+        loose = 0
+        for grams in sets:
+            fp = orc.qgram_fingerprints(S, grams)
+            for metric in ("ham", "lev"):
+                r = orc.bound_violations_fps(S, fp, "weight", 32, metric, q=q)
+                assert r["pairs"] > 0 and r["violations"] == 0, (q, metric, r)
+                loose += orc.bound_violations_fps(S, fp, "weight", 32, metric, q=1)["violations"]
+        assert loose > 0, ("sweep cannot bite", q)
+
+
+def check_fps_filter_is_speedup(orc):
+    """The Sec. 4 method on q-gram fingerprints (bound 2qk) and on binary counts
+    compared by L1 gives the brute-force match lists; L1 lets no more pairs
+    through than the Gray-code Hamming weight does."""
+    w = datagen.english1m(3000, 300)
+    for metric, Q in w.queries.items():
+        for k in (1, 2):
+            rp0, idx0 = orc.match(w.dictionary, Q, k, metric)
+            for q in (2, 3):
+                grams, _ = orc.qgram_map(w.dictionary, q, 32)
+                rp, idx, pairs, surv = orc.filter_match_fps(w.dictionary, Q, k, metric,
+                                                            orc.qgram_fingerprints(w.dictionary, grams),
+                                                            orc.qgram_fingerprints(Q, grams), "weight", 32, q=q)
+                assert np.array_equal(rp, rp0) and np.array_equal(idx, idx0), (metric, k, q)
+                assert rp0[-1] <= surv <= pairs
+            m, _, _ = orc.symbol_map(w.dictionary.chars, "common", 16)
+            rp, idx, pairs, surv = orc.filter_match_fps(
+                w.dictionary, Q, k, metric, orc.fingerprints(w.dictionary, m, "count", 32, gray=False),
+                orc.fingerprints(Q, m, "count", 32, gray=False), "count_l1", 32)
+            assert np.array_equal(rp, rp0) and np.array_equal(idx, idx0), (metric, k, "l1")
+            _, _, pairs_g, surv_g = orc.filter_match(w.dictionary, Q, k, metric, m, "count", 32)
+            assert pairs == pairs_g and rp0[-1] <= surv <= surv_g
+
+
 ALL_CHECKS = [
     check_instance_example, check_run_ran, check_repeated_symbols, check_halves,
     check_count_saturation, check_positions, check_fd_fields, check_symbol_sets,
     check_textbook_distances, check_edit_ball, check_distance_identities, check_verifiers,
     check_match_against_pairs, check_counterexamples, check_filter_decision, check_bound_sweep,
-    check_filter_is_speedup,
+    check_filter_is_speedup, check_count_l1, check_count_l1_sweep, check_qgram_fingerprints, check_qgram_sweep,
+    check_fps_filter_is_speedup,
 ]

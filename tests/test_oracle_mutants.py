@@ -42,6 +42,16 @@ MUTANTS = {
     "rare_order": ("(cnt[rorder[j]] > cnt[c] ||", "(cnt[rorder[j]] < cnt[c] ||"),
     "prune_too_much": ("if (J->prune && (m - n > J->k || n - m > J->k))",
                        "if (J->prune && (m - n >= J->k || n - m > J->k))"),
+    "l1_signed": ("f += ca > cb ? ca - cb : cb - ca;", "f += ca - cb;"),
+    "l1_skips_last_field": ("for (int q = 0; (q + 1) * bits <= width; q++) {",
+                            "for (int q = 0; (q + 2) * bits <= width; q++) {"),
+    "l1_as_weight": ("        return orc_fd_count_l1(a, b, width, bits);\n    return orc_fd",
+                     "        return orc_fd(a, b, ORC_OCC, width, 0, 0);\n    return orc_fd"),
+    "qgram_last_position": ("for (int64_t i = 0; i + q <= n; i++)\n        for (int f = 0;",
+                            "for (int64_t i = 0; i + q < n; i++)\n        for (int f = 0;"),
+    "qgram_tie_break": ("if (cnt[c] > bc) {", "if (cnt[c] >= bc) {"),
+    "qgram_filter_bound_2k": ("int div = 2 * J->qmul;", "int div = 2;"),
+    "qgram_sweep_bound_2k": ("int div = 2 * q;", "int div = 2;"),
 }
 
 
