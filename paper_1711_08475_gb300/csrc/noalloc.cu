@@ -169,31 +169,42 @@ extern "C" int fp_query_noalloc(fp_index *ix, const uint8_t *chars, const int64_
     plan.max_segments = 256 * (2 * k + 1);
     plan.scal = (uint64_t *)(base + O_SCAL);
 
-    const int32_t group[2] = {k, metric};
-    FP_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int32_t), st));
-    FP_CUDA(cudaMemcpyAsync(d_group, group, sizeof(group), cudaMemcpyHostToDevice, st));
-    FP_TRY(bucketize_into(chars, offsets, n_queries, ends[1], nullptr, 1, ix->d_map, ix->P, st, &Q, S, d_err));
-    FilterCfg cfg{};
-    cfg.mode = FP_MODE_TILED;
-    cfg.tq = 256;
-    cfg.v = 4;
-    cfg.k1mix = k == 1;
-    cfg.mma = false;
-    int tq = 0, tw = 0;
-    tile_shape(cfg, ix->P, &tq, &tw);
-    FP_TRY(plan_segments(Q, ix->D, d_group, d_group + 1, tq, tw, &plan, st));
-    FP_TRY(launch_filter(Q, ix->D, plan, ix->P, cfg, surv, MAXS, st, nullptr));
-    FP_TRY(launch_verify(Q, ix->D, surv, plan.scal + 4, MAXS, k, metric, ix->idx_bits, matches, plan.scal + 5,
-                         MAXM, st));
-    const int64_t cap = idx_capacity < MAXM ? idx_capacity : MAXM;
-    FP_TRY(build_csr_into(matches, tmp, S.radix_hist, plan.scal + 5, cap, bits_for_count(n_queries), ix->idx_bits,
-                          n_queries, row_ptr, idx, st));
+    // From the first enqueue on, every exit goes through finish(): a failure
+    // still waits for the work already queued on st, so that no later call
+    // (on any stream) can meet this call's kernels in the shared scratch.
     uint64_t scal[8] = {0};
     int32_t h_err = 0;
-    FP_CUDA(cudaMemcpyAsync(scal, plan.scal, sizeof(scal), cudaMemcpyDeviceToHost, st));
-    FP_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(h_err), cudaMemcpyDeviceToHost, st));
-    FP_CUDA(cudaStreamSynchronize(st));
+    const int64_t cap = idx_capacity < MAXM ? idx_capacity : MAXM;
+    auto enqueue = [&]() -> int {
+        const int32_t group[2] = {k, metric};
+        FP_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int32_t), st));
+        FP_CUDA(cudaMemcpyAsync(d_group, group, sizeof(group), cudaMemcpyHostToDevice, st));
+        FP_TRY(bucketize_into(chars, offsets, n_queries, ends[1], nullptr, 1, ix->d_map, ix->P, st, &Q, S, d_err));
+        FilterCfg cfg{};
+        cfg.mode = FP_MODE_TILED;
+        cfg.tq = 256;
+        cfg.v = 4;
+        cfg.k1mix = k == 1;
+        cfg.mma = false;
+        int tq = 0, tw = 0;
+        tile_shape(cfg, ix->P, &tq, &tw);
+        FP_TRY(plan_segments(Q, ix->D, d_group, d_group + 1, tq, tw, &plan, st));
+        FP_TRY(launch_filter(Q, ix->D, plan, ix->P, cfg, surv, MAXS, st, nullptr));
+        FP_TRY(launch_verify(Q, ix->D, surv, plan.scal + 4, MAXS, k, metric, ix->idx_bits, matches, plan.scal + 5,
+                             MAXM, st));
+        FP_TRY(build_csr_into(matches, tmp, S.radix_hist, plan.scal + 5, cap, bits_for_count(n_queries),
+                              ix->idx_bits, n_queries, row_ptr, idx, st));
+        FP_CUDA(cudaMemcpyAsync(scal, plan.scal, sizeof(scal), cudaMemcpyDeviceToHost, st));
+        FP_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(h_err), cudaMemcpyDeviceToHost, st));
+        return FP_OK;
+    };
+    const int rc = enqueue();
+    const cudaError_t se = cudaStreamSynchronize(st);  // on every path, success or not
+    if (rc != FP_OK) return rc;  // the first error is the one reported
+    if (se != cudaSuccess) return cuda_fail(se, "cudaStreamSynchronize");
     if (h_err) return nfail(FP_E_INVAL, "string longer than 255 bytes or offsets not monotone");
+    if (scal[6])  // the planner's overflow flag: no tile ran, so the lists would be incomplete
+        return nfail(FP_E_OVERFLOW, "fp_query_noalloc: tile plan overflow");
     if ((int64_t)scal[4] > MAXS)
         return nfail(FP_E_OVERFLOW, "fp_query_noalloc: more than FP_NOALLOC_MAX_CANDIDATES pairs passed the filter");
     *n_matches = (int64_t)scal[5];
