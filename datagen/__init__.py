@@ -527,23 +527,34 @@ class Request:
     queries: Strings
 
 
+def poisson_requests(d: Strings, law: StringLaw, seed: int, duration_s: float, rate_qps: float,
+                     max_request: int = 4096, label: str = "req", n_requests: int | None = None):
+    """Requests with sizes U{1..max_request} (50% one-edit Lev mutations of
+    dictionary words) arriving as a Poisson process whose mean pattern rate is
+    ``rate_qps``: every request that arrives within ``duration_s``, or exactly
+    ``n_requests`` requests when that is given."""
+    mean_size = (1 + max_request) / 2.0
+    lam = rate_qps / mean_size
+    n_draw = n_requests if n_requests is not None else max(1, int(math.ceil(duration_s * lam * 1.5)) + 8)
+    gaps = -np.log1p(-uniform(stream_key(seed, f"{label}/gap"), n_draw)) / lam
+    t = np.cumsum(gaps)
+    n_req = n_requests if n_requests is not None else (int(np.searchsorted(t, duration_s, side="right")) or 1)
+    sizes = randint(stream_key(seed, f"{label}/size"), n_req, 1, max_request)
+    pool = make_queries(d, law, seed, f"{label}/pool", int(sizes.sum()), 0.5, "lev")
+    off = _offsets(sizes)
+    reqs = [Request(float(t[i]), pool.subset(np.arange(off[i], off[i + 1]))) for i in range(n_req)]
+    return reqs, pool
+
+
 def serving5m(n_words: int = 5_000_000, duration_s: float = 10.0, rate_qps: float = 5000.0,
-              max_request: int = 4096, seed: int | None = None) -> tuple[Workload, list]:
+              max_request: int = 4096, seed: int | None = None, n_requests: int | None = None
+              ) -> tuple[Workload, list]:
     """5,000,000 URL-like strings; requests with sizes U{1..max_request} arriving
     as a Poisson process whose mean query rate is ``rate_qps``; k=1 Lev."""
     seed = SEEDS["serving5m"] if seed is None else seed
     law = url_law(seed)
     d = law.draw(seed, "dict", n_words)
-    mean_size = (1 + max_request) / 2.0
-    lam = rate_qps / mean_size
-    n_req = max(1, int(math.ceil(duration_s * lam * 1.5)) + 8)
-    gaps = -np.log1p(-uniform(stream_key(seed, "req/gap"), n_req)) / lam
-    t = np.cumsum(gaps)
-    n_req = int(np.searchsorted(t, duration_s, side="right")) or 1
-    sizes = randint(stream_key(seed, "req/size"), n_req, 1, max_request)
-    pool = make_queries(d, law, seed, "req/pool", int(sizes.sum()), 0.5, "lev")
-    off = _offsets(sizes)
-    reqs = [Request(float(t[i]), pool.subset(np.arange(off[i], off[i + 1]))) for i in range(n_req)]
+    reqs, pool = poisson_requests(d, law, seed, duration_s, rate_qps, max_request, "req", n_requests)
     w = Workload("serving5m", seed, d, {"lev": pool}, [("occ", 32, ("lev",))], 1,
-                 {"rate_qps": rate_qps, "n_requests": n_req}, law)
+                 {"rate_qps": rate_qps, "n_requests": len(reqs)}, law)
     return w, reqs

@@ -63,8 +63,24 @@ extern "C" {
  * FP_POS: 0-indexed first position of the symbol mapped to field j,
  *   saturated at 2^p - 1 (also meaning absent), in bits [p j, p j + p); the
  *   leftover W mod p bits are occurrence bits (Sec. 3, "Position");
- *   Hamming only (Theorem 2). */
-typedef enum { FP_OCC = 0, FP_OCC_HALVED = 1, FP_COUNT = 2, FP_POS = 3 } fp_type;
+ *   Hamming only (Theorem 2).
+ * FP_QGRAM: occurrence of q-grams, the paper's future work (Sec. 5): the W
+ *   most frequent q-grams of the dictionary (occurrences over all positions;
+ *   ties go to the smaller q-gram in byte order) each own one bit, set iff
+ *   the q-gram occurs in the string; strings shorter than q get 0.  One edit
+ *   touches at most q q-grams on each side, so F_D grows by at most 2q per
+ *   edit and D >= ceil(F_D / 2q): a pair is rejected iff F_D > 2qk (Eq. 1 is
+ *   q = 1).  Sound for Hamming and Levenshtein.  q = opts->qgram (1..3).
+ * FP_COUNT_L1: the count fingerprint in the paper's own binary code
+ *   (Sec. 3.2), compared by the distance of the counts themselves, F_D =
+ *   sum over fields of |c1 - c2| (the remark after Eq. 1 in Sec. 3.3: the
+ *   Hamming weight of the XOR under-counts, 3 (11) against 1 (01) gives 1
+ *   instead of 2, and over-counts 1 (01) against 2 (10)).  One edit moves
+ *   each of at most two counts by one, so Eq. 1 holds; F_D is never below
+ *   the Gray-coded FP_COUNT distance.  b = 2 only.  Tested on every eligible pair (no
+ *   weight bands: the weight of a binary count field is not bounded by the
+ *   count difference across part boundaries). */
+typedef enum { FP_OCC = 0, FP_OCC_HALVED = 1, FP_COUNT = 2, FP_POS = 3, FP_QGRAM = 4, FP_COUNT_L1 = 5 } fp_type;
 
 /* Distances of Sec. 1. */
 typedef enum { FP_HAM = 0, FP_LEV = 1 } fp_metric;
@@ -82,9 +98,10 @@ typedef struct {
                                   pattern also gets a 32-bit occurrence fingerprint over the 32 most
                                   frequent symbols, and a pair survives only if both fingerprints
                                   pass Eq. 1 (each is sound alone, Theorem 1).  FP_COUNT at 32 bits
-                                  only; used by fp_query / fp_query_ex (batched runs, the server and
-                                  fp_query_noalloc test the count fingerprint alone).  0 = off */
+                                  only; used by fp_query / fp_query_ex, batched runs and the server
+                                  (fp_query_noalloc tests the count fingerprint alone).  0 = off */
     const int8_t *custom_map;  /* host, [256]: field of each byte value or -1; only for FP_SET_CUSTOM */
+    int32_t qgram;             /* q for FP_QGRAM, 1..3; 0 = 2.  The set must be FP_SET_COMMON */
 } fp_build_opts;
 
 /* Query execution forms. */
@@ -106,7 +123,11 @@ typedef struct {
                                 FP8 MMA dot products decide Eq. 1 exactly (128 patterns x 1024 words per
                                 tile; tile_queries and words_per_thread do not apply; position
                                 fingerprints keep the population-count kernel) */
+    int32_t flags;           /* FP_OPT_* bits; 0 = none */
 } fp_query_opts;
+/* fp_plan_create: run the pipeline launch by launch instead of capturing it
+ * into a CUDA graph (for timing the stages, or where graphs are unwanted). */
+#define FP_OPT_NO_GRAPH 1
 
 typedef struct {
     int64_t n_queries;
@@ -131,6 +152,7 @@ typedef struct {
     int32_t sigma;        /* tracked fields */
     int64_t bucket_count[256]; /* words per length */
     int64_t device_bytes; /* device memory held by the index */
+    int32_t qgram;        /* q of FP_QGRAM (1 for the other types) */
 } fp_index_info;
 
 typedef struct fp_index fp_index;
@@ -150,7 +172,9 @@ typedef struct fp_result fp_result;
  *   type: fp_type; width_bits: 16 or 32.
  *   opts: NULL for defaults.
  * Errors: FP_E_INVAL (bad pointer/size/width/offsets/length),
- * FP_E_UNSUPPORTED (layout does not fit: b*1 > W, p*1 > W), FP_E_NOMEM,
+ * FP_E_UNSUPPORTED (layout does not fit: b*1 > W, p*1 > W; FP_QGRAM with a
+ * set other than FP_SET_COMMON, combined types or more than 2^32 - 1
+ * dictionary bytes), FP_E_NOMEM,
  * FP_E_CUDA.  Synchronises cuda_stream before returning. */
 FP_API int fp_build(const uint8_t *chars, const int64_t *offsets, int64_t n_words, int type, int width_bits,
              const fp_build_opts *opts, void *cuda_stream, fp_index **out);
@@ -162,6 +186,7 @@ FP_API int fp_build(const uint8_t *chars, const int64_t *offsets, int64_t n_word
  *   chars, offsets: host or device, same rules as fp_build.
  *   k: 0..15; metric: fp_metric.
  *   opts: NULL for FP_MODE_TILED with the tuned tile.
+ * FP_QGRAM indexes reject a pair iff F_D > 2qk; the other types use Eq. 1.
  * Errors: FP_E_INVAL, FP_E_UNSUPPORTED (FP_OCC_HALVED or FP_POS index with
  * FP_LEV: Eq. 1 does not hold for them), FP_E_NOMEM, FP_E_CUDA.
  * Synchronises cuda_stream once at the end (to size the result). */
@@ -199,8 +224,9 @@ FP_API int fp_query_ex(fp_index *ix, const uint8_t *chars, const int64_t *offset
  * loss, *n_used = non-matching samples, grad = mean gradient.  params, masks,
  * match, grad: host or device.
  *
- * fp_learn_map: Adam over epochs of mini-batches, tau annealed geometrically
- * from tau0 to tau1; map_out[256] (host) = argmax field per printable symbol,
+ * fp_learn_map: Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) over
+ * epochs of mini-batches, tau annealed geometrically from tau0 (first epoch)
+ * to tau1 (last; a single epoch uses tau1); map_out[256] (host) = argmax field per printable symbol,
  * -1 elsewhere; params_out (optional, host or device) = trained parameters;
  * loss_curve (optional, host) = mean loss per epoch.  Apply the map with
  * fp_set_symbol_map. */
@@ -212,6 +238,8 @@ typedef struct {
     float tau1;      /* 0 = 0.1 */
     float beta;      /* 0 = 2.0 */
     uint64_t seed;   /* 0 = 1711 */
+    const float *init_params; /* host or device, fp_mlp_param_count() floats: the starting parameters
+                                 (NULL = seeded initialisation: W uniform in +-1/sqrt(fan-in), b = 0) */
 } fp_learn_opts;
 FP_API int fp_mlp_param_count(void);
 FP_API int fp_sample_pairs(fp_index *ix, const uint8_t *chars, const int64_t *offsets, int64_t n_queries, int k,
@@ -269,9 +297,11 @@ FP_API int fp_query_batched(fp_index *ix, const uint8_t *chars, const int64_t *o
  * fp_plan_run of a shape (patterns, bytes, batches, distinct (k, metric)
  * groups) records the device pipeline into a CUDA graph on the plan's own
  * stream; later runs of the same shape replay it with one graph launch.
- * opts: tile_queries and variant as for fp_query_ex; mode FP_MODE_PLAIN turns
- * the graph off.  Runs of one plan must not overlap (one host thread at a
- * time); results do not refer to the plan's memory. */
+ * opts: tile_queries and variant as for fp_query_ex; flags FP_OPT_NO_GRAPH
+ * turns the graph off; mode must be FP_MODE_TILED or FP_MODE_FUSED (both mean
+ * the fused pipeline; the plain scan is not a plan form, FP_E_UNSUPPORTED).
+ * Runs of one plan must not overlap (one host thread at a time); results do
+ * not refer to the plan's memory. */
 FP_API int fp_plan_create(fp_index *ix, int64_t max_queries, int64_t max_chars, int32_t max_batches,
                           const fp_query_opts *opts, fp_plan **out);
 FP_API int fp_plan_run(fp_plan *plan, const uint8_t *chars, const int64_t *offsets, int64_t n_queries,
@@ -395,9 +425,15 @@ FP_API void fp_result_free(fp_result *r);
 FP_API int fp_index_info_get(const fp_index *ix, fp_index_info *info);
 /* The symbol map in use: map[c] = field of byte c or -1 (host, [256]). */
 FP_API int fp_index_map(const fp_index *ix, int8_t *map_out);
+/* The q-grams of an FP_QGRAM index in field order: grams_out (host, at
+ * least 32 * 3 bytes) gets field f's q bytes at [f q, f q + q); *n_grams the
+ * number of fields used, *q the gram length.  FP_E_UNSUPPORTED for other
+ * types. */
+FP_API int fp_index_qgrams(const fp_index *ix, uint8_t *grams_out, int32_t *n_grams, int32_t *q);
 /* Replaces the symbol map (Sec. 3.2: the c -> q mapping) and rebuilds every
  * dictionary fingerprint on the device.  Any many-to-one map keeps Eq. 1
- * valid for FP_OCC and FP_COUNT.  map: host, [256], values < sigma or -1. */
+ * valid for FP_OCC and FP_COUNT.  map: host, [256], values < sigma or -1.
+ * FP_E_UNSUPPORTED for FP_QGRAM indexes (their fields are q-grams). */
 FP_API int fp_set_symbol_map(fp_index *ix, const int8_t *map);
 /* Fingerprints (Sec. 3.2) of arbitrary strings under the index's type, width
  * and map, in input order.  chars/offsets host or device; out_fp host or

@@ -16,7 +16,8 @@ from .native import (FP_COUNT, FP_HAM, FP_LEV, FP_MODE_FUSED, FP_MODE_PLAIN, FP_
                      FP_OCC_HALVED, FP_POS, FP_SET_COMMON, FP_SET_CUSTOM, FP_SET_MIXED, FP_SET_RARE, FpError,
                      check, load)
 
-TYPES = {"occ": FP_OCC, "occh": FP_OCC_HALVED, "count": FP_COUNT, "pos": FP_POS}
+TYPES = {"occ": FP_OCC, "occh": FP_OCC_HALVED, "count": FP_COUNT, "pos": FP_POS, "qgram": native.FP_QGRAM,
+         "count_l1": native.FP_COUNT_L1}
 METRICS = {"ham": FP_HAM, "lev": FP_LEV}
 SETS = {"common": FP_SET_COMMON, "rare": FP_SET_RARE, "mixed": FP_SET_MIXED, "custom": FP_SET_CUSTOM}
 MODES = {"tiled": FP_MODE_TILED, "plain": FP_MODE_PLAIN, "fused": FP_MODE_FUSED}
@@ -133,6 +134,14 @@ class Index:
         check(load().fp_index_map(self._h, m.ctypes.data), "fp_index_map")
         return m
 
+    def qgrams(self) -> np.ndarray:
+        """The q-grams of a q-gram index in field order, uint8[fields, q] (fp_index_qgrams)."""
+        L = load()
+        buf = np.zeros(96, dtype=np.uint8)
+        n, q = ctypes.c_int32(0), ctypes.c_int32(0)
+        check(L.fp_index_qgrams(self._h, buf.ctypes.data, ctypes.byref(n), ctypes.byref(q)), "fp_index_qgrams")
+        return buf[:n.value * q.value].reshape(n.value, q.value)
+
     def set_symbol_map(self, m):
         m = np.ascontiguousarray(m, dtype=np.int8)
         assert m.shape == (256,)
@@ -162,7 +171,8 @@ class Index:
 
 
 def fp_build(chars, offsets=None, fp_type: str = "occ", width: int = 32, symbol_set: str = "common",
-             count_bits: int = 2, pos_bits: int = 3, custom_map=None, stream=None, combined: bool = False) -> Index:
+             count_bits: int = 2, pos_bits: int = 3, custom_map=None, stream=None, combined: bool = False,
+             qgram: int = 0) -> Index:
     """Builds the resident index (fp_build in include/fp.h)."""
     L = load()
     chars, offsets, n = _strings(chars, offsets)
@@ -171,6 +181,7 @@ def fp_build(chars, offsets=None, fp_type: str = "occ", width: int = 32, symbol_
     o.count_bits = count_bits
     o.pos_bits = pos_bits
     o.combined = 1 if combined else 0
+    o.qgram = qgram
     keep = None
     if custom_map is not None:
         keep = np.ascontiguousarray(custom_map, dtype=np.int8)
@@ -238,7 +249,8 @@ class Plan:
     def __init__(self, index: Index, max_queries: int, max_chars: int, max_batches: int, tile_queries: int = 0,
                  variant: int = 0, graph: bool = True):
         o = native.fp_query_opts()
-        o.mode = FP_MODE_FUSED if graph else FP_MODE_PLAIN
+        o.mode = FP_MODE_FUSED
+        o.flags = 0 if graph else native.FP_OPT_NO_GRAPH
         o.tile_queries = tile_queries
         o.variant = variant
         h = ctypes.c_void_p()
@@ -399,11 +411,17 @@ def fp_mlp_loss_grad(params, fields: int, tau: float, beta: float, k: int, masks
 
 
 def fp_learn_map(fields: int, masks, match, k: int = 1, epochs: int = 0, batch: int = 0, lr: float = 0.0,
-                 tau0: float = 0.0, tau1: float = 0.0, beta: float = 0.0, seed: int = 0, stream=None):
+                 tau0: float = 0.0, tau1: float = 0.0, beta: float = 0.0, seed: int = 0, stream=None,
+                 init_params=None):
     """Trains the map on the GPU: (map int8[256], params float32, loss per epoch)."""
     L = load()
     o = native.fp_learn_opts()
     o.epochs, o.batch, o.lr, o.tau0, o.tau1, o.beta, o.seed = epochs, batch, lr, tau0, tau1, beta, seed
+    init = None
+    if init_params is not None:
+        init = np.ascontiguousarray(init_params, dtype=np.float32)
+        assert init.size == fp_mlp_param_count()
+        o.init_params = init.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
     m = np.ascontiguousarray(masks, dtype=np.uint64)
     mt = np.ascontiguousarray(match, dtype=np.uint8)
     mp = np.zeros(256, np.int8)

@@ -227,9 +227,12 @@ int fp_build(const uint8_t *chars, const int64_t *offsets, int64_t n_words, int 
     fp_build_opts o{};
     if (opts) o = *opts;
     FpParams P;
-    int rc = make_params(type, width_bits, o.count_bits, o.pos_bits, &P);
+    if (type == FP_QGRAM && (o.qgram < 0 || o.qgram > 3)) return fail(FP_E_UNSUPPORTED, "q-grams: q must be 1..3");
+    int rc = make_params(type, width_bits, o.count_bits, o.pos_bits, &P, o.qgram);
     if (rc != FP_OK) return fail(rc, "fingerprint type / width / b / p not supported");
     if (o.set < FP_SET_COMMON || o.set > FP_SET_CUSTOM) return fail(FP_E_INVAL, "bad symbol set");
+    if (type == FP_QGRAM && o.set != FP_SET_COMMON)
+        return fail(FP_E_UNSUPPORTED, "q-gram fingerprints take the most frequent q-grams only");
     if (o.combined != 0 && o.combined != 1) return fail(FP_E_INVAL, "combined must be 0 or 1");
     if (o.combined && (type != FP_COUNT || width_bits != 32))
         return fail(FP_E_UNSUPPORTED, "combined types: count fingerprints of 32 bits only");
@@ -259,7 +262,23 @@ int fp_build(const uint8_t *chars, const int64_t *offsets, int64_t n_words, int 
         rc = cuda_fail(cudaGetLastError(), "cudaMemsetAsync");
         goto fail_out;
     }
-    if (o.set == FP_SET_CUSTOM) {
+    if (type == FP_QGRAM) {  // fields are q-grams: no symbol map, a q-gram table instead
+        if (S.total > (int64_t)0xFFFFFFFFLL) {
+            rc = fail(FP_E_UNSUPPORTED, "q-gram fingerprints: at most 2^32 - 1 dictionary bytes");
+            goto fail_out;
+        }
+        memset(ix->h_map, 0xFF, 256);
+        if (cudaMemsetAsync(ix->d_map, 0xFF, 256, st) != cudaSuccess ||
+            cudaMemsetAsync(ix->d_counts, 0, 256 * sizeof(unsigned long long), st) != cudaSuccess ||
+            cudaMalloc((void **)&ix->d_gmap, (size_t)1 << (8 * P.q)) != cudaSuccess) {
+            rc = cuda_fail(cudaErrorMemoryAllocation, "q-gram table");
+            goto fail_out;
+        }
+        rc = qgram_map(S.chars, S.off, n_words, P.q, P.sigma, ix->d_gmap, ix->h_gram, &ix->n_grams, st);
+        if (rc != FP_OK) goto fail_out;
+        P.gmap = ix->d_gmap;
+        ix->P = P;
+    } else if (o.set == FP_SET_CUSTOM) {
         memcpy(ix->h_map, o.custom_map, 256);
         if (cudaMemcpy(ix->d_map, ix->h_map, 256, cudaMemcpyHostToDevice) != cudaSuccess) {
             rc = cuda_fail(cudaGetLastError(), "map copy");
@@ -272,7 +291,7 @@ int fp_build(const uint8_t *chars, const int64_t *offsets, int64_t n_words, int 
     }
     rc = bucketize(S.chars, S.off, n_words, S.total, nullptr, 1, ix->d_map, P, false, st, &ix->D, d_err);
     if (rc != FP_OK) goto fail_out;
-    if (P.type != FP_POS) {  // weight order of every bucket (population-count fingerprints)
+    if (banded_type(P.type)) {  // weight order of every bucket (population-count fingerprints)
         if (cudaMalloc((void **)&ix->d_wstart, sizeof(int32_t) * 256 * (size_t)(cell_count(P.width) + 1)) !=
             cudaSuccess) {
             rc = cuda_fail(cudaGetLastError(), "weight table");
@@ -306,7 +325,8 @@ int fp_build(const uint8_t *chars, const int64_t *offsets, int64_t n_words, int 
             rc = cuda_fail(e, "fp_build");
             goto fail_out;
         }
-        if (o.set != FP_SET_CUSTOM && cudaMemcpy(ix->h_map, ix->d_map, 256, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        if (o.set != FP_SET_CUSTOM && type != FP_QGRAM &&
+            cudaMemcpy(ix->h_map, ix->d_map, 256, cudaMemcpyDeviceToHost) != cudaSuccess) {
             rc = cuda_fail(cudaGetLastError(), "map copy");
             goto fail_out;
         }
@@ -317,7 +337,8 @@ int fp_build(const uint8_t *chars, const int64_t *offsets, int64_t n_words, int 
     }
     ix->device_bytes = ix->D.n_slots * (4 + 1 + 4) + (ix->D.n_slots + FP_SLACK_SLOTS) * (P.width / 8) +
                        ix->D.str_bytes + STR_SLACK + 256 * 9 + (ix->D.fp2 ? ix->D.n_slots * 4 + 256 : 0) +
-                       (ix->d_wstart ? 256 * 4 * (int64_t)(cell_count(P.width) + 1) : 0);
+                       (ix->d_wstart ? 256 * 4 * (int64_t)(cell_count(P.width) + 1) : 0) +
+                       (ix->d_gmap ? (int64_t)1 << (8 * P.q) : 0);
     S.release(st);
     cudaFreeAsync(d_err, st);
     cudaStreamSynchronize(st);
@@ -338,6 +359,7 @@ void fp_free(fp_index *ix) {
     if (ix->d_counts) cudaFree(ix->d_counts);
     if (ix->d_wstart) cudaFree(ix->d_wstart);
     if (ix->d_map2) cudaFree(ix->d_map2);
+    if (ix->d_gmap) cudaFree(ix->d_gmap);
     delete ix;
 }
 
@@ -353,6 +375,17 @@ int fp_index_info_get(const fp_index *ix, fp_index_info *info) {
     info->sigma = ix->P.sigma;
     for (int L = 0; L < 256; L++) info->bucket_count[L] = ix->h_count[L];
     info->device_bytes = ix->device_bytes;
+    info->qgram = ix->P.q;
+    return FP_OK;
+}
+
+int fp_index_qgrams(const fp_index *ix, uint8_t *grams_out, int32_t *n_grams, int32_t *q) {
+    if (!ix || !grams_out || !n_grams || !q) return fail(FP_E_INVAL, "null argument");
+    if (ix->P.type != FP_QGRAM) return fail(FP_E_UNSUPPORTED, "not a q-gram index");
+    *q = ix->P.q;
+    *n_grams = ix->n_grams;
+    for (int f = 0; f < ix->n_grams; f++)
+        for (int j = 0; j < ix->P.q; j++) grams_out[f * ix->P.q + j] = (uint8_t)(ix->h_gram[f] >> (8 * (ix->P.q - 1 - j)));
     return FP_OK;
 }
 
@@ -364,6 +397,7 @@ int fp_index_map(const fp_index *ix, int8_t *map_out) {
 
 int fp_set_symbol_map(fp_index *ix, const int8_t *map) {
     if (!ix || !map) return fail(FP_E_INVAL, "null argument");
+    if (ix->P.type == FP_QGRAM) return fail(FP_E_UNSUPPORTED, "the fields of a q-gram index are q-grams");
     for (int c = 0; c < 256; c++)
         if (map[c] < -1 || map[c] >= ix->P.sigma) return fail(FP_E_INVAL, "map field out of range");
     memcpy(ix->h_map, map, 256);
@@ -537,7 +571,7 @@ int fp_query_ex(fp_index *ix, const uint8_t *chars, const int64_t *offsets, int6
         plan_scratch_place(&R.plan, R.plan_scratch, ucap, R.Q.nbins);
     }
     TRY(plan_segments(R.Q, ix->D, R.d_group, R.d_group + 1, tq, tw, &R.plan, st, band ? ix->d_wstart : nullptr,
-                      ix->P.width));
+                      ix->P.width, ix->P.q));
     // survivor capacity: exact pair count when the host saw the lengths, else a bound
     if (S.host_checked) {
         pairs_bound = host_pairs(ix, S.host_len_hist, k, metric);

@@ -12,28 +12,36 @@
 // read once, left to right; a symbol c whose field is q = map[c] sets or
 // updates field q.  Sec. 3 (symbol sets): the map takes the most / least
 // frequent symbols of the collection, or half of each.
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace fpk {
 
-int make_params(int type, int width, int b, int p, FpParams *o) {
+int make_params(int type, int width, int b, int p, FpParams *o, int q) {
     if (width != 16 && width != 32) return FP_E_INVAL;
-    if (type < FP_OCC || type > FP_POS) return FP_E_INVAL;
+    if (type < FP_OCC || type > FP_COUNT_L1) return FP_E_INVAL;
     if (b <= 0) b = 2;
     if (p <= 0) p = 3;
+    if (q <= 0) q = 2;
     if (b > 8 || p > 8) return FP_E_UNSUPPORTED;
+    if (type == FP_QGRAM && q > 3) return FP_E_UNSUPPORTED;
+    if (type == FP_COUNT_L1 && b != 2) return FP_E_UNSUPPORTED;  // the filter's L1 arithmetic is for 2-bit counts
     FpParams P{};
     P.type = type;
     P.width = width;
     P.b = b;
     P.p = p;
+    P.q = type == FP_QGRAM ? q : 1;
     switch (type) {
         case FP_OCC: P.sigma = width; break;
+        case FP_QGRAM: P.sigma = width; break;
         case FP_OCC_HALVED: P.sigma = width / 2; break;
         case FP_COUNT:
+        case FP_COUNT_L1:
             if (b > width) return FP_E_UNSUPPORTED;
             P.sigma = width / b;
-            for (int q = 0; q < P.sigma; q++) P.count_top |= 1u << (b * q + b - 1);
+            for (int f = 0; f < P.sigma; f++) P.count_top |= 1u << (b * f + b - 1);
             break;
         case FP_POS:
             if (p > width) return FP_E_UNSUPPORTED;
@@ -50,9 +58,25 @@ int make_params(int type, int width, int b, int p, FpParams *o) {
     return FP_OK;
 }
 
+static int grid_for(int64_t n, int threads = 256, int cap = 8192) {
+    int64_t g = (n + threads - 1) / threads;
+    return (int)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+// Counts one launch and returns its launch error as a status.
+static int launched(const char *name) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? FP_OK : cuda_fail(e, name);
+}
+
 // ---------------------------------------------------------------------------
 // fingerprint of one string, byte by byte (Sec. 3.2)
 // ---------------------------------------------------------------------------
+// For FP_QGRAM (the future work of Sec. 5) a field is a q-gram, not a symbol:
+// put() keeps the last q bytes as a rolling code (first byte most
+// significant) and, from the q-th byte on, sets the bit of the q-gram ending
+// here (P.gmap: code -> field or -1).  The other types map one byte.
 template <int TYPE>
 struct FpAcc {
     uint32_t v, seen;
@@ -60,13 +84,25 @@ struct FpAcc {
         seen = 0;
         v = (TYPE == FP_POS) ? (P.pos_low | P.pos_high) : 0u;
     }
+    // byte ch at position pos of a string of length len (smap: byte -> field)
+    __device__ __forceinline__ void put(uint32_t ch, const int8_t *smap, int pos, int len, const FpParams &P) {
+        if (TYPE == FP_QGRAM) {
+            seen = (seen << 8) | ch;  // rolling code of the last q bytes
+            if (pos + 1 >= P.q) {
+                const int f = P.gmap[seen & ((1u << (8 * P.q)) - 1u)];
+                if (f >= 0) v |= 1u << f;
+            }
+        } else {
+            add(smap[ch], pos, len, P);
+        }
+    }
     __device__ __forceinline__ void add(int q, int pos, int len, const FpParams &P) {
         if (q < 0) return;
         if (TYPE == FP_OCC) {
             v |= 1u << q;
         } else if (TYPE == FP_OCC_HALVED) {
             v |= 1u << (2 * q + (pos >= (len >> 1) ? 1 : 0));
-        } else if (TYPE == FP_COUNT) {
+        } else if (TYPE == FP_COUNT || TYPE == FP_COUNT_L1) {
             uint32_t sat = (1u << P.b) - 1u;
             uint32_t c = (v >> (P.b * q)) & sat;
             if (c < sat) v += 1u << (P.b * q);
@@ -86,6 +122,7 @@ struct FpAcc {
     __device__ __forceinline__ uint32_t finish(const FpParams &P) {
         uint32_t r = v;
         if (TYPE == FP_COUNT) r = r ^ ((r >> 1) & ~P.count_top);  // per-field reflected Gray code
+        // FP_COUNT_L1 keeps the paper's plain binary counts
         if (P.width == 16) r &= 0xFFFFu;
         return r;
     }
@@ -180,6 +217,110 @@ int symbol_map(const uint8_t *d_chars, int64_t total, int set, int sigma, int8_t
 }
 
 // ---------------------------------------------------------------------------
+// q-gram statistics (Sec. 5 future work: fingerprints over q-grams)
+// ---------------------------------------------------------------------------
+// One thread per string: every q-gram occurrence (positions 0 .. len - q).
+__global__ void k_qgram_hist(const uint8_t *__restrict__ chars, const int64_t *__restrict__ off, int64_t n, int q,
+                             uint32_t *__restrict__ counts) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint8_t *s = chars + off[i];
+        const int64_t L = off[i + 1] - off[i];
+        uint32_t code = 0;
+        for (int64_t j = 0; j < L; j++) {
+            code = (code << 8) | s[j];
+            if (j + 1 >= q) atomicAdd(&counts[code & ((1u << (8 * q)) - 1u)], 1u);
+        }
+    }
+}
+
+// The most frequent q-gram not yet taken: key (count << 24) | (2^24 - 1 -
+// code), so the largest key has the highest count and, among equal counts,
+// the smallest code.  Block maxima meet in one atomicMax.
+__global__ void __launch_bounds__(256) k_qgram_argmax(const uint32_t *__restrict__ counts, int64_t ncodes,
+                                                      unsigned long long *__restrict__ best) {
+    unsigned long long m = 0;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncodes; c += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = counts[c];
+        if (v) {
+            const unsigned long long key = ((unsigned long long)v << 24) | (unsigned long long)(0xFFFFFFu - (uint32_t)c);
+            m = key > m ? key : m;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, m, o);
+        m = y > m ? y : m;
+    }
+    __shared__ unsigned long long s_m[8];
+    if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; w++) m = s_m[w] > m ? s_m[w] : m;
+        if (m) atomicMax(best, m);
+    }
+}
+
+// Takes the winner of round f: field f, and its count is cleared so the next
+// round skips it.  codes[f] = the code, or ~0 when no q-gram is left.
+__global__ void k_qgram_take(unsigned long long *__restrict__ best, int f, uint32_t *__restrict__ counts,
+                             int8_t *__restrict__ gmap, uint32_t *__restrict__ codes) {
+    const unsigned long long m = *best;
+    if (m == 0) {
+        codes[f] = 0xFFFFFFFFu;
+    } else {
+        const uint32_t code = 0xFFFFFFu - (uint32_t)(m & 0xFFFFFFu);
+        codes[f] = code;
+        gmap[code] = (int8_t)f;
+        counts[code] = 0;
+    }
+    *best = 0;
+}
+
+int qgram_map(const uint8_t *d_chars, const int64_t *d_off, int64_t n, int q, int sigma, int8_t *d_gmap,
+              uint32_t *h_codes, int *n_used, cudaStream_t st) {
+    if (q < 1 || q > 3 || sigma < 0 || sigma > 32) return fail(FP_E_INVAL, "q-gram map: q must be 1..3");
+    const int64_t ncodes = (int64_t)1 << (8 * q);
+    uint32_t *counts = nullptr, *codes = nullptr;
+    unsigned long long *best = nullptr;
+    int rc = FP_OK;
+    cudaError_t e;
+    if ((e = cudaMallocAsync((void **)&counts, sizeof(uint32_t) * (size_t)ncodes, st)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&codes, sizeof(uint32_t) * 32, st)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&best, sizeof(unsigned long long), st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)ncodes, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(best, 0, sizeof(unsigned long long), st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(d_gmap, 0xFF, (size_t)ncodes, st)) != cudaSuccess) {
+        rc = cuda_fail(e, "q-gram map: scratch");
+    }
+    if (rc == FP_OK && n > 0) {
+        k_qgram_hist<<<grid_for(n, 256, 8192), 256, 0, st>>>(d_chars, d_off, n, q, counts);
+        rc = launched("k_qgram_hist");
+    }
+    const int g = (int)std::min<int64_t>(1024, (ncodes + 255) / 256);
+    for (int f = 0; rc == FP_OK && f < sigma; f++) {
+        k_qgram_argmax<<<g, 256, 0, st>>>(counts, ncodes, best);
+        if ((rc = launched("k_qgram_argmax")) != FP_OK) break;
+        k_qgram_take<<<1, 1, 0, st>>>(best, f, counts, d_gmap, codes);
+        rc = launched("k_qgram_take");
+    }
+    *n_used = 0;
+    if (rc == FP_OK) {
+        uint32_t h[32];
+        if ((e = cudaMemcpyAsync(h, codes, sizeof(uint32_t) * (size_t)(sigma > 0 ? sigma : 1), cudaMemcpyDeviceToHost,
+                                 st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+            rc = cuda_fail(e, "q-gram map");
+        } else {
+            for (int f = 0; f < sigma && h[f] != 0xFFFFFFFFu; f++) h_codes[(*n_used)++] = h[f];
+        }
+    }
+    if (counts) cudaFreeAsync(counts, st);
+    if (codes) cudaFreeAsync(codes, st);
+    if (best) cudaFreeAsync(best, st);
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
 // bucketing
 // ---------------------------------------------------------------------------
 __global__ void k_bin_keys(const int64_t *__restrict__ off, int64_t n, const int32_t *__restrict__ group,
@@ -235,7 +376,7 @@ __global__ void k_bin_keys_cells(const int64_t *__restrict__ off, const uint8_t 
             const uint8_t *src = chars + off[i];
             FpAcc<TYPE> acc;
             acc.init(P);
-            for (int pos = 0; pos < (int)L; pos++) acc.add(smap[src[pos]], pos, (int)L, P);
+            for (int pos = 0; pos < (int)L; pos++) acc.put(src[pos], smap, pos, (int)L, P);
             cell = fp_cell(acc.finish(P), P.width);
         }
         keys[i] = ((((uint64_t)bin << CELL_BITS) | (uint64_t)cell) << 32) | (uint64_t)i;
@@ -330,7 +471,7 @@ __global__ void __launch_bounds__(256) k_scatter_fp(const uint64_t *__restrict__
                 if (pos < L) {
                     uint32_t ch = src[pos];
                     w[j >> 2] |= ch << (8 * (j & 3));
-                    acc.add(smap[ch], pos, L, P);
+                    acc.put(ch, smap, pos, L, P);
                 }
             }
             dst[c0 >> 4] = make_uint4(w[0], w[1], w[2], w[3]);
@@ -358,7 +499,7 @@ __global__ void __launch_bounds__(256) k_refingerprint(Bucketed B, const int8_t 
 #pragma unroll
             for (int j = 0; j < 16; j++) {
                 int pos = c0 + j;
-                if (pos < L) acc.add(smap[(w[j >> 2] >> (8 * (j & 3))) & 0xFF], pos, L, P);
+                if (pos < L) acc.put((w[j >> 2] >> (8 * (j & 3))) & 0xFF, smap, pos, L, P);
             }
         }
         store_fp(B.fp, P.width, s, acc.finish(P));
@@ -379,28 +520,32 @@ __global__ void __launch_bounds__(256) k_fingerprint_list(const uint8_t *__restr
         const uint8_t *src = chars + off[i];
         FpAcc<TYPE> acc;
         acc.init(P);
-        for (int64_t pos = 0; pos < L; pos++) acc.add(smap[src[pos]], (int)pos, (int)L, P);
+        for (int64_t pos = 0; pos < L; pos++) acc.put(src[pos], smap, (int)pos, (int)L, P);
         out[i] = acc.finish(P);
     }
 }
 
-static int grid_for(int64_t n, int threads = 256, int cap = 8192) {
-    int64_t g = (n + threads - 1) / threads;
-    return (int)(g < 1 ? 1 : (g > cap ? cap : g));
+// Calls f(std::integral_constant<int, TYPE>) for the fingerprint type.
+template <class F>
+static void by_type(int type, F &&f) {
+    switch (type) {
+        case FP_OCC: f(std::integral_constant<int, FP_OCC>{}); break;
+        case FP_OCC_HALVED: f(std::integral_constant<int, FP_OCC_HALVED>{}); break;
+        case FP_COUNT: f(std::integral_constant<int, FP_COUNT>{}); break;
+        case FP_QGRAM: f(std::integral_constant<int, FP_QGRAM>{}); break;
+        case FP_COUNT_L1: f(std::integral_constant<int, FP_COUNT_L1>{}); break;
+        default: f(std::integral_constant<int, FP_POS>{}); break;
+    }
 }
+
 
 int fingerprint_list(const uint8_t *d_chars, const int64_t *d_off, int64_t n, const int8_t *d_map,
                      const FpParams &P, uint32_t *d_out, cudaStream_t st) {
     if (n <= 0) return FP_OK;
     int g = grid_for(n);
-    switch (P.type) {
-        case FP_OCC: k_fingerprint_list<FP_OCC><<<g, 256, 0, st>>>(d_chars, d_off, n, d_map, P, d_out); break;
-        case FP_OCC_HALVED:
-            k_fingerprint_list<FP_OCC_HALVED><<<g, 256, 0, st>>>(d_chars, d_off, n, d_map, P, d_out);
-            break;
-        case FP_COUNT: k_fingerprint_list<FP_COUNT><<<g, 256, 0, st>>>(d_chars, d_off, n, d_map, P, d_out); break;
-        default: k_fingerprint_list<FP_POS><<<g, 256, 0, st>>>(d_chars, d_off, n, d_map, P, d_out); break;
-    }
+    by_type(P.type, [&](auto tt) {
+        k_fingerprint_list<decltype(tt)::value><<<g, 256, 0, st>>>(d_chars, d_off, n, d_map, P, d_out);
+    });
     FP_LAUNCHED("k_fingerprint_list");
     return FP_OK;
 }
@@ -439,12 +584,6 @@ static int dev_alloc(void **p, size_t bytes, bool so, cudaStream_t st) {
 // weight_order sorts the real slots of each bin by (weight, current slot)
 // and, on request, records per bin the first slot of every weight.
 
-// Counts one launch and returns its launch error as a status.
-static int launched(const char *name) {
-    g_launches.fetch_add(1, std::memory_order_relaxed);
-    const cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? FP_OK : cuda_fail(e, name);
-}
 
 __device__ __forceinline__ int slot_cell(const void *fp, int width, int64_t s) {
     return fp_cell(width == 16 ? (uint32_t)((const uint16_t *)fp)[s] : ((const uint32_t *)fp)[s], width);
@@ -535,7 +674,7 @@ __global__ void k_weight_table(const uint64_t *__restrict__ keys, const int32_t 
 }
 
 int weight_order(Bucketed *B, const FpParams &P, int32_t *d_wstart, cudaStream_t st) {
-    if (P.type == FP_POS || B->n <= 0) {
+    if (!banded_type(P.type) || B->n <= 0) {
         if (d_wstart)
             FP_CUDA(cudaMemsetAsync(d_wstart, 0, sizeof(int32_t) * (size_t)B->nbins * (cell_count(P.width) + 1), st));
         return FP_OK;
@@ -598,7 +737,7 @@ int bucketize(const uint8_t *d_chars, const int64_t *d_off, int64_t n, int64_t t
               const int32_t *d_group, int32_t n_groups, const int8_t *d_map, const FpParams &P,
               bool so, cudaStream_t st, Bucketed *out, int32_t *d_err, bool cells) {
     Bucketed B;
-    const int shift = cells && P.type != FP_POS ? CELL_BITS : 0;
+    const int shift = cells && banded_type(P.type) ? CELL_BITS : 0;
     B.stream_ordered = so;
     B.n = n;
     B.nbins = 256 * (n_groups < 1 ? 1 : n_groups);
@@ -645,13 +784,11 @@ int bucketize(const uint8_t *d_chars, const int64_t *d_off, int64_t n, int64_t t
             const size_t sh = nbins * sizeof(int32_t);
             if (shift == 0)
                 k_bin_keys<<<g, 256, sh, st>>>(d_off, n, d_group, nbins, keys, hist, d_err);
-            else if (P.type == FP_OCC)
-                k_bin_keys_cells<FP_OCC><<<g, 256, sh, st>>>(d_off, d_chars, n, d_group, nbins, d_map, P, keys, hist, d_err);
-            else if (P.type == FP_OCC_HALVED)
-                k_bin_keys_cells<FP_OCC_HALVED><<<g, 256, sh, st>>>(d_off, d_chars, n, d_group, nbins, d_map, P, keys, hist,
-                                                                    d_err);
             else
-                k_bin_keys_cells<FP_COUNT><<<g, 256, sh, st>>>(d_off, d_chars, n, d_group, nbins, d_map, P, keys, hist, d_err);
+                by_type(P.type, [&](auto tt) {
+                    k_bin_keys_cells<decltype(tt)::value>
+                        <<<g, 256, sh, st>>>(d_off, d_chars, n, d_group, nbins, d_map, P, keys, hist, d_err);
+                });
             g_launches++;
             if ((e = cudaGetLastError()) != cudaSuccess) { rc = cuda_fail(e, "k_bin_keys"); goto fail; }
         }
@@ -665,20 +802,10 @@ int bucketize(const uint8_t *d_chars, const int64_t *d_off, int64_t n, int64_t t
             rc = radix_sort_u64(keys, keys2, nullptr, n, 32, 32 + shift + bin_bits, st, &sorted);
             if (rc != FP_OK) goto fail;
             int g = grid_for(n, 256, 8192);
-            switch (P.type) {
-                case FP_OCC:
-                    k_scatter_fp<FP_OCC><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B.b_start, ustart, str16, B, shift);
-                    break;
-                case FP_OCC_HALVED:
-                    k_scatter_fp<FP_OCC_HALVED><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B.b_start, ustart, str16, B, shift);
-                    break;
-                case FP_COUNT:
-                    k_scatter_fp<FP_COUNT><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B.b_start, ustart, str16, B, shift);
-                    break;
-                default:
-                    k_scatter_fp<FP_POS><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B.b_start, ustart, str16, B, shift);
-                    break;
-            }
+            by_type(P.type, [&](auto tt) {
+                k_scatter_fp<decltype(tt)::value>
+                    <<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B.b_start, ustart, str16, B, shift);
+            });
             g_launches++;
             if ((e = cudaGetLastError()) != cudaSuccess) { rc = cuda_fail(e, "k_scatter_fp"); goto fail; }
         }
@@ -741,12 +868,7 @@ int second_fingerprints(Bucketed *B, const int8_t *d_map2, const FpParams &P2, c
 int refingerprint(Bucketed *B, const int8_t *d_map, const FpParams &P, cudaStream_t st) {
     if (B->n_slots <= 0) return FP_OK;
     int g = grid_for(B->n_slots, 256, 8192);
-    switch (P.type) {
-        case FP_OCC: k_refingerprint<FP_OCC><<<g, 256, 0, st>>>(*B, d_map, P); break;
-        case FP_OCC_HALVED: k_refingerprint<FP_OCC_HALVED><<<g, 256, 0, st>>>(*B, d_map, P); break;
-        case FP_COUNT: k_refingerprint<FP_COUNT><<<g, 256, 0, st>>>(*B, d_map, P); break;
-        default: k_refingerprint<FP_POS><<<g, 256, 0, st>>>(*B, d_map, P); break;
-    }
+    by_type(P.type, [&](auto tt) { k_refingerprint<decltype(tt)::value><<<g, 256, 0, st>>>(*B, d_map, P); });
     FP_LAUNCHED("k_refingerprint");
     return FP_OK;
 }
@@ -762,7 +884,7 @@ int bucketize_into(const uint8_t *d_chars, const int64_t *d_off, int64_t n, int6
                    const int32_t *d_group, int32_t n_groups, const int8_t *d_map, const FpParams &P, cudaStream_t st,
                    Bucketed *B, const BucketScratch &S, int32_t *d_err, bool cells) {
     const int nbins = 256 * (n_groups < 1 ? 1 : n_groups);
-    const int shift = cells && P.type != FP_POS ? CELL_BITS : 0;
+    const int shift = cells && banded_type(P.type) ? CELL_BITS : 0;
     const int64_t slots_ub = n + (int64_t)(SLOT_ALIGN - 1) * nbins;
     const int64_t str_ub = total_chars + 15 * n;
     const size_t fpw = P.width == 16 ? 2 : 4;
@@ -780,13 +902,11 @@ int bucketize_into(const uint8_t *d_chars, const int64_t *d_off, int64_t n, int6
         const size_t sh = nbins * sizeof(int32_t);
         if (shift == 0)
             k_bin_keys<<<g, 256, sh, st>>>(d_off, n, d_group, nbins, S.keys, S.hist, d_err);
-        else if (P.type == FP_OCC)
-            k_bin_keys_cells<FP_OCC><<<g, 256, sh, st>>>(d_off, d_chars, n, d_group, nbins, d_map, P, S.keys, S.hist, d_err);
-        else if (P.type == FP_OCC_HALVED)
-            k_bin_keys_cells<FP_OCC_HALVED><<<g, 256, sh, st>>>(d_off, d_chars, n, d_group, nbins, d_map, P, S.keys, S.hist,
-                                                                d_err);
         else
-            k_bin_keys_cells<FP_COUNT><<<g, 256, sh, st>>>(d_off, d_chars, n, d_group, nbins, d_map, P, S.keys, S.hist, d_err);
+            by_type(P.type, [&](auto tt) {
+                k_bin_keys_cells<decltype(tt)::value>
+                    <<<g, 256, sh, st>>>(d_off, d_chars, n, d_group, nbins, d_map, P, S.keys, S.hist, d_err);
+            });
         FP_LAUNCHED("k_bin_keys");
     }
     k_plan_bins<<<1, 1024, 0, st>>>(S.hist, nbins, B->b_start, B->b_count, S.ustart, S.str16, S.tot);
@@ -797,20 +917,10 @@ int bucketize_into(const uint8_t *d_chars, const int64_t *d_off, int64_t n, int6
         uint64_t *sorted = S.keys;
         FP_TRY(radix_sort_u64_into(S.keys, S.keys2, S.radix_hist, nullptr, n, 32, 32 + shift + bin_bits, st, &sorted));
         int g = grid_for(n, 256, 8192);
-        switch (P.type) {
-            case FP_OCC:
-                k_scatter_fp<FP_OCC><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B->b_start, S.ustart, S.str16, *B, shift);
-                break;
-            case FP_OCC_HALVED:
-                k_scatter_fp<FP_OCC_HALVED><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B->b_start, S.ustart, S.str16, *B, shift);
-                break;
-            case FP_COUNT:
-                k_scatter_fp<FP_COUNT><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B->b_start, S.ustart, S.str16, *B, shift);
-                break;
-            default:
-                k_scatter_fp<FP_POS><<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B->b_start, S.ustart, S.str16, *B, shift);
-                break;
-        }
+        by_type(P.type, [&](auto tt) {
+            k_scatter_fp<decltype(tt)::value>
+                <<<g, 256, 0, st>>>(sorted, n, d_off, d_chars, d_map, P, B->b_start, S.ustart, S.str16, *B, shift);
+        });
         FP_LAUNCHED("k_scatter_fp");
     }
     B->n_slots = slots_ub;

@@ -58,8 +58,15 @@ struct FpParams {
     uint32_t pos_low;    // low p-1 bits of every position field
     uint32_t pos_high;   // top bit of every position field
     uint32_t pos_occ;    // occurrence bits above the position fields
+    int32_t q;           // q-gram length (FP_QGRAM); 1 for the other types.  A pair is
+                         // rejected iff F_D > 2 q k (Eq. 1 is q = 1)
+    const int8_t *gmap;  // FP_QGRAM: device table q-gram code (first byte most significant) -> field or -1
 };
-int make_params(int type, int width, int b, int p, FpParams *out);
+int make_params(int type, int width, int b, int p, FpParams *out, int q = 0);
+// Types whose F_D is the population count of the XOR and whose buckets are
+// kept in weight-cell order (weight bands); position fingerprints and the
+// count L1 distance are compared field by field and are not banded.
+inline bool banded_type(int type) { return type != FP_POS && type != FP_COUNT_L1; }
 
 // ---------------------------------------------------------------------------
 // a bucketed set of strings on the device (dictionary or query batch)
@@ -125,6 +132,13 @@ int weight_order(Bucketed *b, const FpParams &fp, int32_t *d_wstart, cudaStream_
 // Symbol statistics (Sec. 3 symbol sets): byte counts and the field map.
 int symbol_map(const uint8_t *d_chars, int64_t total, int set, int sigma, int8_t *d_map,
                unsigned long long *d_counts, cudaStream_t st);
+// q-gram fingerprints (Sec. 5): counts every q-gram (1 <= q <= 3) of the n
+// strings and writes d_gmap[code] = field for the sigma most frequent ones
+// (ties: smaller code; -1 elsewhere; d_gmap has 256^q entries).  h_codes
+// (host, sigma) gets the codes in field order, *n_used how many occur.
+// Synchronises st.
+int qgram_map(const uint8_t *d_chars, const int64_t *d_off, int64_t n, int q, int sigma, int8_t *d_gmap,
+              uint32_t *h_codes, int *n_used, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // radix sort of 64-bit keys (stable LSD) and scans
@@ -176,10 +190,11 @@ struct FilterCfg {
 // d_wstart (optional): the dictionary's cell table (weight_order); when
 // given, the patterns' bins must be in cell order too, and each tile of tq
 // patterns gets segments per dictionary bucket restricted to the cells
-// Eq. 1 can pass.  width: fingerprint width in bits.
+// Eq. 1 can pass.  width: fingerprint width in bits.  tmul: a pair can pass
+// only if F_D <= 2 tmul k (q for q-gram fingerprints, else 1).
 int plan_segments(const Bucketed &q, const Bucketed &d, const int32_t *d_group_k,
                   const int32_t *d_group_metric, int tq, int tw, QueryPlan *plan, cudaStream_t st,
-                  const int32_t *d_wstart = nullptr, int width = 32);
+                  const int32_t *d_wstart = nullptr, int width = 32, int tmul = 1);
 
 int launch_filter(const Bucketed &q, const Bucketed &d, const QueryPlan &plan, const FpParams &fp,
                   const FilterCfg &cfg, uint64_t *surv, int64_t surv_cap, cudaStream_t st,
@@ -264,6 +279,9 @@ struct fp_index {
     fpk::Bucketed D;
     int8_t *d_map = nullptr;
     int8_t h_map[256];
+    int8_t *d_gmap = nullptr;     // FP_QGRAM: q-gram code -> field (256^q entries)
+    uint32_t h_gram[32];          // FP_QGRAM: the q-gram of every field (code, first byte most significant)
+    int n_grams = 0;
     int32_t *d_wstart = nullptr;  // weight order of the buckets (null: position fingerprints, no weight bands)
     // combined types: a second, 32-bit occurrence fingerprint over the 32 most
     // frequent symbols (null map: off)

@@ -60,12 +60,8 @@ constexpr int FT_QUEUE = 256;  // queued (lane, tile query) hits per warp
 #ifndef FT_UNROLL
 #define FT_UNROLL 1  // groups of four queries unrolled in the loop over a partial batch
 #endif
-#ifndef FT_SPLIT_FULL
-// 0: one copy of the pattern loop for whole and short tiles; a short tile's
-// fingerprints past its end are tested like the others and masked in the
-// exact re-test (a hit there only costs a re-test).  1: a masked copy of the
-// loop for short tiles.
-#define FT_SPLIT_FULL 0
+#ifndef FT_COLS
+#define FT_COLS 2  // 128-word columns each warp scans per tile (the tile's setup is shared by them)
 #endif
 #define FT_STR(x) #x
 #define FT_UNROLL_PRAGMA(n) _Pragma(FT_STR(unroll n))
@@ -77,21 +73,45 @@ struct PosMasks {
     uint32_t low, high, occ;
 };
 
-// F_D of one XOR word holding one 32-bit fingerprint.
-template <bool POS>
-__device__ __forceinline__ uint32_t fd32(uint32_t x, const PosMasks &M) {
-    if (!POS) return __popc(x);
-    // a field is nonzero iff its top bit or the carry out of its low p-1 bits is set
-    uint32_t s = (x & M.low) + M.low;
-    return __popc(((s | x) & M.high) | (x & M.occ));
+// Kinds of F_D (Sec. 3.3): the Hamming weight of the XOR (occurrence,
+// occurrence halved, Gray-coded count, q-grams); the number of differing
+// p-bit position fields plus the weight of the occurrence bits (position);
+// the L1 distance of 2-bit binary-coded counts (count in the paper's code).
+constexpr int FDK_POPC = 0, FDK_POS = 1, FDK_L1 = 2;
+
+// F_D of a dictionary fingerprint w and a pattern fingerprint q (32-bit).
+// L1 of 2-bit binary counts: with x = w ^ q, a field differs by x0 + 2 x1,
+// except that x1 = x0 = 1 means 3 against 0 when the word's two bits are
+// equal and 2 against 1 (a difference of 1) when they differ; so F_D =
+// popc(x) + popc(x & high bits) - 2 popc(low bits where x1, x0 and w1 ^ w0
+// are set).
+template <int FDK>
+__device__ __forceinline__ uint32_t fd32(uint32_t w, uint32_t q, const PosMasks &M) {
+    const uint32_t x = w ^ q;
+    if (FDK == FDK_POPC) return __popc(x);
+    if (FDK == FDK_POS) {
+        // a field is nonzero iff its top bit or the carry out of its low p-1 bits is set
+        uint32_t s = (x & M.low) + M.low;
+        return __popc(((s | x) & M.high) | (x & M.occ));
+    }
+    const uint32_t c = x & (x >> 1) & (w ^ (w >> 1)) & 0x55555555u;
+    return __popc(x) + __popc(x & 0xAAAAAAAAu) - 2u * __popc(c);
 }
 
-// F_D of the two 16-bit fingerprints packed in one XOR word (masks replicated
-// in both halves; per-field carries never cross a field, so never the halves).
-template <bool POS>
-__device__ __forceinline__ void fd16x2(uint32_t x, const PosMasks &M, uint32_t &lo, uint32_t &hi) {
+// F_D of the two 16-bit fingerprints packed in one 32-bit word of each side
+// (masks replicated in both halves; position carries and count fields never
+// cross a field, so never the halves).
+template <int FDK>
+__device__ __forceinline__ void fd16x2(uint32_t w, uint32_t q, const PosMasks &M, uint32_t &lo, uint32_t &hi) {
+    const uint32_t x = w ^ q;
+    if (FDK == FDK_L1) {
+        const uint32_t h = x & 0xAAAAAAAAu, c = x & (x >> 1) & (w ^ (w >> 1)) & 0x55555555u;
+        lo = __popc(x & 0xFFFFu) + __popc(h & 0xFFFFu) - 2u * __popc(c & 0xFFFFu);
+        hi = __popc(x >> 16) + __popc(h >> 16) - 2u * __popc(c >> 16);
+        return;
+    }
     uint32_t z = x;
-    if (POS) {
+    if (FDK == FDK_POS) {
         uint32_t s = (x & M.low) + M.low;
         z = ((s | x) & M.high) | (x & M.occ);
     }
@@ -109,6 +129,7 @@ struct FilterArgs {
     uint64_t surv_cap;
     PosMasks M;
     int tq;
+    int tmul;  // a pair passes iff F_D <= 2 tmul k: tmul = q for q-gram fingerprints, 1 otherwise (Eq. 1)
     // fused form: survivors are verified in the kernel and only matches leave it
     const uint8_t *q_len, *d_len;
     const uint32_t *q_row16, *d_row16;
@@ -198,26 +219,26 @@ __device__ __forceinline__ int find_segment_warp(const Segment *seg, int nseg, u
     return lo;
 }
 
-// Thread layout of a tile.  Fingerprints arrive in 128-bit vectors of G
-// fingerprints (G = 4 for 32-bit, 8 for 16-bit); vector r of thread t holds
-// the tile's fingerprints r*(T*G) + t*G + (0..G-1) (T = FT_THREADS), so one warp-wide load
-// reads 512 contiguous bytes.  Fingerprint i of a thread (0 <= i < NF) is at
-// tile offset (i/G)*(T*G) + t*G + i%G; relative to the warp's first slot it
-// is (i/G)*(T*G) + lane*G + i%G.
+// Lane layout of a column (one warp's load: 32 lanes x NF fingerprints).
+// Fingerprints arrive in 128-bit vectors of G fingerprints (G = 4 for 32-bit,
+// 8 for 16-bit); vector r of lane l holds the column's fingerprints
+// r*(32*G) + l*G + (0..G-1), so one warp-wide load reads 512 contiguous
+// bytes.  Fingerprint i of a lane (0 <= i < NF) is at column offset
+// (i/G)*(32*G) + lane*G + i%G.
 template <int G>
 __device__ __forceinline__ uint32_t lane_offset(int i, int lane) {
-    return (uint32_t)(i / G) * (uint32_t)(FT_THREADS * G) + (uint32_t)lane * G + (uint32_t)(i % G);
+    return (uint32_t)(i / G) * (uint32_t)(32 * G) + (uint32_t)lane * G + (uint32_t)(i % G);
 }
 
 // All F_D values of a thread's fingerprints against query word q.
-template <int W, int V, bool POS, int NF>
+template <int W, int V, int FDK, int NF>
 __device__ __forceinline__ void all_fd(const uint32_t (&w)[V], uint32_t q, const PosMasks &M, uint32_t (&F)[NF]) {
     if (W == 32) {
 #pragma unroll
-        for (int v = 0; v < V; v++) F[v] = fd32<POS>(w[v] ^ q, M);
+        for (int v = 0; v < V; v++) F[v] = fd32<FDK>(w[v], q, M);
     } else {
 #pragma unroll
-        for (int v = 0; v < V; v++) fd16x2<POS>(w[v] ^ q, M, F[2 * v], F[2 * v + 1]);
+        for (int v = 0; v < V; v++) fd16x2<FDK>(w[v], q, M, F[2 * v], F[2 * v + 1]);
     }
 }
 
@@ -288,7 +309,7 @@ __device__ __forceinline__ uint32_t min_tree(const uint32_t *v) {
 // happen.  K1MIX (32-bit occ/occh/count, k = 1): the last quarter of the words
 // is tested with clear2 instead of the population count (passes iff clear2 == 0,
 // i.e. iff (clear2 | 2) <= 2, so it joins the same minimum).
-template <int W, int V, bool POS, bool FULL, bool K1MIX>
+template <int W, int V, int FDK, bool FULL, bool K1MIX>
 __device__ __forceinline__ int32_t pass_sign(const uint32_t (&w)[V], uint32_t q, const PosMasks &M,
                                              uint32_t invalid, uint32_t T) {
     if (K1MIX) {
@@ -315,9 +336,9 @@ __device__ __forceinline__ int32_t pass_sign(const uint32_t (&w)[V], uint32_t q,
 #pragma unroll
         for (int v = 0; v < V; v++) {
             if (W == 32) {
-                f[v] = fd32<POS>(w[v] ^ q, M);
+                f[v] = fd32<FDK>(w[v], q, M);
             } else {
-                fd16x2<POS>(w[v] ^ q, M, f[2 * v], f[2 * v + 1]);
+                fd16x2<FDK>(w[v], q, M, f[2 * v], f[2 * v + 1]);
             }
         }
         if (!FULL) {
@@ -331,13 +352,13 @@ __device__ __forceinline__ int32_t pass_sign(const uint32_t (&w)[V], uint32_t q,
 
 // Four queries (one 128-bit shared load) against the thread's fingerprints;
 // each test's sign bit is shifted into the hit mask.
-template <int W, int V, bool POS, bool FULL, bool K1MIX>
+template <int W, int V, int FDK, bool FULL, bool K1MIX>
 __device__ __forceinline__ uint32_t four_queries(const uint32_t (&w)[V], uint4 q4, const PosMasks &M, uint32_t invalid,
                                                  uint32_t T, uint32_t hits) {
-    const int32_t h0 = pass_sign<W, V, POS, FULL, K1MIX>(w, q4.x, M, invalid, T);
-    const int32_t h1 = pass_sign<W, V, POS, FULL, K1MIX>(w, q4.y, M, invalid, T);
-    const int32_t h2 = pass_sign<W, V, POS, FULL, K1MIX>(w, q4.z, M, invalid, T);
-    const int32_t h3 = pass_sign<W, V, POS, FULL, K1MIX>(w, q4.w, M, invalid, T);
+    const int32_t h0 = pass_sign<W, V, FDK, FULL, K1MIX>(w, q4.x, M, invalid, T);
+    const int32_t h1 = pass_sign<W, V, FDK, FULL, K1MIX>(w, q4.y, M, invalid, T);
+    const int32_t h2 = pass_sign<W, V, FDK, FULL, K1MIX>(w, q4.z, M, invalid, T);
+    const int32_t h3 = pass_sign<W, V, FDK, FULL, K1MIX>(w, q4.w, M, invalid, T);
     hits = __funnelshift_l((uint32_t)h0, hits, 1);
     hits = __funnelshift_l((uint32_t)h1, hits, 1);
     hits = __funnelshift_l((uint32_t)h2, hits, 1);
@@ -361,7 +382,7 @@ __device__ __forceinline__ void make_room(const FilterArgs &A, uint64_t *stage, 
 // count), i.e. (owner lane, tile query), fetches the owner's fingerprints with
 // shuffles and stages every pair of that query and those fingerprints that
 // passes Eq. 1.
-template <int W, int V, bool POS, bool FULL, bool FUSED, bool COMB>
+template <int W, int V, int FDK, bool FULL, bool FUSED, bool COMB>
 __device__ __forceinline__ void retest_round(const FilterArgs &A, const uint32_t *s_q, const uint16_t *queue,
                                              uint32_t first, uint32_t count, uint32_t q0, const uint32_t (&w)[V],
                                              uint32_t invalid, uint32_t T, uint32_t wbase, uint64_t *stage,
@@ -378,7 +399,7 @@ __device__ __forceinline__ void retest_round(const FilterArgs &A, const uint32_t
     const uint32_t inv = FULL ? 0u : __shfl_sync(0xffffffffu, invalid, src);
     if (has) {
         uint32_t F[NF];
-        all_fd<W, V, POS, NF>(ws, s_q[jq], A.M, F);
+        all_fd<W, V, FDK, NF>(ws, s_q[jq], A.M, F);
 #pragma unroll
         for (int i = 0; i < NF; i++)
             if (F[i] <= T && (FULL || !((inv >> i) & 1u)))
@@ -398,7 +419,7 @@ __device__ __forceinline__ void retest_round(const FilterArgs &A, const uint32_t
 // hits), and the warp re-tests the queue in rounds of 32 whenever it holds a
 // full round, so nearly every round keeps all 32 lanes busy; the last partial
 // round runs when the tile ends (the fingerprints in registers belong to it).
-template <int W, int V, bool POS, bool FULL, bool K1MIX, bool FUSED, bool COMB>
+template <int W, int V, int FDK, bool FULL, bool K1MIX, bool FUSED, bool COMB>
 __device__ __forceinline__ void scan_tile(const FilterArgs &A, const uint32_t *s_q, uint32_t nq, uint32_t q0,
                                           const uint32_t (&w)[V], uint32_t invalid, uint32_t T, uint32_t wbase,
                                           uint64_t *stage, uint32_t *cnt, uint16_t *queue, uint32_t *qcnt, int lane,
@@ -413,12 +434,12 @@ __device__ __forceinline__ void scan_tile(const FilterArgs &A, const uint32_t *s
         if (!FUSED && jn == 32u) {  // a whole batch: fully unrolled (the fused form is faster without)
 #pragma unroll
             for (uint32_t jj = 0; jj < 32u; jj += 4)
-                hits = four_queries<W, V, POS, FULL || !FT_SPLIT_FULL, K1MIX>(w, s_q4[(jb + jj) >> 2], A.M, invalid, T,
+                hits = four_queries<W, V, FDK, true, K1MIX>(w, s_q4[(jb + jj) >> 2], A.M, invalid, T,
                                                                               hits);
         } else {
             FT_UNROLL_PRAGMA(FT_UNROLL)
             for (uint32_t jj = 0; jj < jn; jj += 4)
-                hits = four_queries<W, V, POS, FULL || !FT_SPLIT_FULL, K1MIX>(w, s_q4[(jb + jj) >> 2], A.M, invalid, T,
+                hits = four_queries<W, V, FDK, true, K1MIX>(w, s_q4[(jb + jj) >> 2], A.M, invalid, T,
                                                                               hits);
         }
         hits &= ~((1u << (jn4 - jn)) - 1u);  // queries past nq in the last group of four
@@ -435,7 +456,7 @@ __device__ __forceinline__ void scan_tile(const FilterArgs &A, const uint32_t *s
             uint32_t done = 0;
             for (; qn - done >= 32u; done += 32u) {
                 make_room<NF, FUSED>(A, stage, cnt, lane, k, metric);
-                retest_round<W, V, POS, FULL, FUSED, COMB>(A, s_q, queue, done, 32u, q0, w, invalid, T, wbase, stage, cnt,
+                retest_round<W, V, FDK, FULL, FUSED, COMB>(A, s_q, queue, done, 32u, q0, w, invalid, T, wbase, stage, cnt,
                                                      lane, k, metric);
             }
             if (done) {  // move the rest (< 32) to the front
@@ -456,7 +477,7 @@ __device__ __forceinline__ void scan_tile(const FilterArgs &A, const uint32_t *s
                 make_room<NF, FUSED>(A, stage, cnt, lane, k, metric);
                 if (mine) {
                     uint32_t F[NF];
-                    all_fd<W, V, POS, NF>(w, s_q[jb + jj], A.M, F);
+                    all_fd<W, V, FDK, NF>(w, s_q[jb + jj], A.M, F);
 #pragma unroll
                     for (int i = 0; i < NF; i++)
                         if (F[i] <= T && (FULL || !((invalid >> i) & 1u)))
@@ -476,7 +497,7 @@ __device__ __forceinline__ void scan_tile(const FilterArgs &A, const uint32_t *s
     const uint32_t qn = *qcnt;
     if (qn) {
         make_room<NF, FUSED>(A, stage, cnt, lane, k, metric);
-        retest_round<W, V, POS, FULL, FUSED, COMB>(A, s_q, queue, 0u, qn, q0, w, invalid, T, wbase, stage, cnt, lane, k,
+        retest_round<W, V, FDK, FULL, FUSED, COMB>(A, s_q, queue, 0u, qn, q0, w, invalid, T, wbase, stage, cnt, lane, k,
                                              metric);
         __syncwarp();
         if (lane == 0) *qcnt = 0;
@@ -484,24 +505,35 @@ __device__ __forceinline__ void scan_tile(const FilterArgs &A, const uint32_t *s
     }
 }
 
-template <int W, int V, bool POS, bool FUSED>
+template <int W, int V, int FDK, bool FUSED>
 constexpr int ft_min_blocks() {
-    return FUSED ? FT_FUSED_MIN_BLOCKS : ((W == 32 && V == 4 && !POS) ? FT_MAIN_MIN_BLOCKS : FT_MIN_BLOCKS);
+    return FUSED ? FT_FUSED_MIN_BLOCKS : ((W == 32 && V == 4 && FDK == FDK_POPC) ? FT_MAIN_MIN_BLOCKS : FT_MIN_BLOCKS);
 }
 
 // W: fingerprint width; V: 32-bit words per thread (multiple of 4).
 // COMB: combined types (second fingerprints checked for every pass).
-template <int W, int V, bool POS, bool K1MIX, bool FUSED, bool COMB>
-__global__ void __launch_bounds__(FT_THREADS, (ft_min_blocks<W, V, POS, FUSED>())) k_filter_tiled(FilterArgs A) {
+//
+// A tile is tq patterns x FT_WARPS * FT_COLS columns of 32 * NF words.  Its
+// setup is done once per block: thread 0 claims it, warp 0 finds its segment
+// and stages the patterns in shared memory.  The block's work in the tile is
+// a list of items (column, batch of 32 patterns), split evenly over the warps
+// in order: a warp loads a column's fingerprints into registers once and
+// scans its consecutive batches against them.  A short tile (the end of a
+// run of weight cells) has fewer columns, and its items spread the same way,
+// so no warp idles while there is work.
+template <int W, int V, int FDK, bool K1MIX, bool FUSED, bool COMB>
+__global__ void __launch_bounds__(FT_THREADS, (ft_min_blocks<W, V, FDK, FUSED>())) k_filter_tiled(FilterArgs A) {
     constexpr int G = (W == 32) ? 4 : 8;             // fingerprints per 128-bit vector
-    constexpr int NF = (W == 32) ? V : 2 * V;        // fingerprints per thread
-    constexpr int TW = NF * FT_THREADS;              // fingerprints per tile
+    constexpr int NF = (W == 32) ? V : 2 * V;        // fingerprints per lane
+    constexpr int CW = NF * 32;                      // fingerprints per column
+    constexpr int TW = CW * FT_WARPS * FT_COLS;      // fingerprints per tile
     __shared__ __align__(16) uint32_t s_q[FT_MAX_TQ];
     __shared__ uint64_t s_stage[FT_WARPS][FT_STAGE];
     __shared__ uint32_t s_cnt[FT_WARPS];
     __shared__ uint16_t s_queue[FT_WARPS][FT_QUEUE];
     __shared__ uint32_t s_qcnt[FT_WARPS];
     __shared__ uint64_t s_tile;
+    __shared__ Segment s_seg;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nseg = (int)A.scal[0];
     const uint64_t ntiles = A.scal[1];
@@ -519,66 +551,63 @@ __global__ void __launch_bounds__(FT_THREADS, (ft_min_blocks<W, V, POS, FUSED>()
         __syncthreads();
         const uint64_t tile = s_tile;
         if (tile >= ntiles) break;
-        const Segment S = A.seg[find_segment_warp(A.seg, nseg, tile, lane)];
-        const uint64_t local = tile - S.tile_begin;
-        const uint32_t qt = (uint32_t)(local / S.n_dtiles), dt = (uint32_t)(local % S.n_dtiles);
-        const uint32_t q0 = S.q_start + qt * (uint32_t)A.tq;
-        const uint32_t nq = min((uint32_t)A.tq, S.q_count - qt * (uint32_t)A.tq);
-        const uint32_t w0 = S.d_start + dt * (uint32_t)TW;      // first fingerprint slot of the tile
-        const uint32_t nw = min((uint32_t)TW, S.d_count - dt * (uint32_t)TW);
-        const uint32_t T = 2u * (uint32_t)S.k;
-        for (uint32_t j = threadIdx.x; j < nq; j += FT_THREADS) {
-            uint32_t f = (W == 32) ? A.qfp32[q0 + j] : (uint32_t)A.qfp16[q0 + j];
-            s_q[j] = (W == 32) ? f : (f | (f << 16));
+        if (warp == 0) {  // the tile's segment and patterns
+            const Segment S = A.seg[find_segment_warp(A.seg, nseg, tile, lane)];
+            const uint32_t local = (uint32_t)(tile - S.tile_begin);
+            const uint32_t qt = S.n_qtiles == 1u ? 0u : local / S.n_dtiles;
+            const uint32_t q0 = S.q_start + qt * (uint32_t)A.tq;
+            const uint32_t nq = min((uint32_t)A.tq, S.q_count - qt * (uint32_t)A.tq);
+            for (uint32_t j = lane; j < nq; j += 32) {
+                uint32_t f = (W == 32) ? A.qfp32[q0 + j] : (uint32_t)A.qfp16[q0 + j];
+                s_q[j] = (W == 32) ? f : (f | (f << 16));
+            }
+            if (lane == 0) s_seg = S;
         }
         __syncthreads();
-        // A short tile (the end of a run of weight cells) has fingerprints for
-        // nch < FT_WARPS warps' columns; the block then splits its patterns into
-        // FT_WARPS / nchp slices (nchp: nch rounded up to a power of two) and warp
-        // (c, s) scans column c against slice s, so that no warp idles
-        // while there is work.
-        const uint32_t nch = min((nw + 32u * G - 1u) / (32u * G), (uint32_t)FT_WARPS);
-        const uint32_t nchp = nch <= 1u ? 1u : (nch <= 2u ? 2u : (nch <= 4u ? 4u : 8u));
-        const uint32_t col = (uint32_t)warp % nchp, slice = (uint32_t)warp / nchp, nsl = FT_WARPS / nchp;
-        const uint32_t qs = (((nq + nsl - 1u) / nsl) + 31u) & ~31u;  // whole batches of 32 patterns
-        const uint32_t qa = min(slice * qs, nq), qn = min(qs, nq - qa);
-        // the thread's dictionary fingerprints, as 32-bit words
-        uint32_t w[V];
-        const uint32_t word0 = (W == 32) ? w0 : w0 / 2;  // w0 is a multiple of 8 slots
+        const uint32_t local = (uint32_t)(tile - s_seg.tile_begin);
+        const uint32_t ndt = s_seg.n_dtiles;
+        const uint32_t qt = s_seg.n_qtiles == 1u ? 0u : local / ndt;
+        const uint32_t dt = local - qt * ndt;
+        const uint32_t q0 = s_seg.q_start + qt * (uint32_t)A.tq;
+        const uint32_t nq = min((uint32_t)A.tq, s_seg.q_count - qt * (uint32_t)A.tq);
+        const uint32_t w0 = s_seg.d_start + dt * (uint32_t)TW;  // first fingerprint slot of the tile
+        const uint32_t nw = min((uint32_t)TW, s_seg.d_count - dt * (uint32_t)TW);
+        const int k = s_seg.k, metric = s_seg.metric;
+        const uint32_t T = 2u * (uint32_t)k * (uint32_t)A.tmul;
+        const uint32_t nb = (nq + 31u) >> 5;                         // batches of 32 patterns
+        const uint32_t nit = ((nw + CW - 1u) / CW) * nb;             // items (column, batch)
+        const uint32_t it1 = (uint32_t)(warp + 1) * nit / FT_WARPS;
+        for (uint32_t it = (uint32_t)warp * nit / FT_WARPS; it < it1;) {
+            const uint32_t col = it / nb, b0 = it - col * nb, b1 = min(nb, b0 + (it1 - it));
+            const uint32_t wbase = w0 + col * CW;
+            // the column's fingerprints, as 32-bit words (wbase is a multiple of 8
+            // slots; slots past the tile end are readable slack or the next run)
+            uint32_t w[V];
+            const uint32_t word0 = (W == 32) ? wbase : wbase / 2;
 #pragma unroll
-        for (int r = 0; r < V / 4; r++) {
-            const uint4 x = *reinterpret_cast<const uint4 *>(A.dfp + word0 + r * (FT_THREADS * 4) + (col * 32u + lane) * 4);
-            w[4 * r + 0] = x.x;
-            w[4 * r + 1] = x.y;
-            w[4 * r + 2] = x.z;
-            w[4 * r + 3] = x.w;
-        }
-        const uint32_t wrel = col * 32u * G;
-        const uint32_t wbase = w0 + wrel;
-        const uint32_t nvalid = nw > wrel ? nw - wrel : 0u;
-        // fingerprints past the tile end must never pass
-        uint32_t invalid = 0;  // bit i: fingerprint i lies past the tile end
+            for (int r = 0; r < V / 4; r++) {
+                const uint4 x = *reinterpret_cast<const uint4 *>(A.dfp + word0 + r * (32 * 4) + lane * 4);
+                w[4 * r + 0] = x.x;
+                w[4 * r + 1] = x.y;
+                w[4 * r + 2] = x.z;
+                w[4 * r + 3] = x.w;
+            }
+            const uint32_t nvalid = nw - col * CW;
+            uint32_t invalid = 0;  // bit i: fingerprint i lies past the tile end (masked in the exact re-test)
 #pragma unroll
-        for (int i = 0; i < NF; i++)
-            if (lane_offset<G>(i, lane) >= nvalid) invalid |= 1u << i;
-        if (nvalid == 0u || qn == 0u) {
-            // nothing for this warp in a short tile
-        } else if (K1MIX && T != 2u) {  // a k = 1 variant given another k: exact general path
-            if (FT_SPLIT_FULL && nw == (uint32_t)TW)
-                scan_tile<W, V, POS, true, false, FUSED, COMB>(A, s_q + qa, qn, q0 + qa, w, invalid, T, wbase, stage, cnt, queue, qcnt, lane,
-                                                           S.k, S.metric);
+            for (int i = 0; i < NF; i++)
+                if (lane_offset<G>(i, lane) >= nvalid) invalid |= 1u << i;
+            const uint32_t qa = b0 * 32u, qn = min(nq, b1 * 32u) - qa;
+            if (K1MIX && T != 2u)  // a k = 1 variant given another k: exact general path
+                scan_tile<W, V, FDK, false, false, FUSED, COMB>(A, s_q + qa, qn, q0 + qa, w, invalid, T, wbase, stage,
+                                                                cnt, queue, qcnt, lane, k, metric);
             else
-                scan_tile<W, V, POS, false, false, FUSED, COMB>(A, s_q + qa, qn, q0 + qa, w, invalid, T, wbase, stage, cnt, queue, qcnt, lane,
-                                                           S.k, S.metric);
-        } else if (FT_SPLIT_FULL && nw == (uint32_t)TW) {
-            scan_tile<W, V, POS, true, K1MIX, FUSED, COMB>(A, s_q + qa, qn, q0 + qa, w, invalid, T, wbase, stage, cnt, queue, qcnt, lane,
-                                                           S.k, S.metric);
-        } else {
-            scan_tile<W, V, POS, false, K1MIX, FUSED, COMB>(A, s_q + qa, qn, q0 + qa, w, invalid, T, wbase, stage, cnt, queue, qcnt, lane,
-                                                           S.k, S.metric);
+                scan_tile<W, V, FDK, false, K1MIX, FUSED, COMB>(A, s_q + qa, qn, q0 + qa, w, invalid, T, wbase, stage,
+                                                                cnt, queue, qcnt, lane, k, metric);
+            it += b1 - b0;
         }
         // fused: the next tile may have another (k, metric), so verify what is staged
-        if (FUSED) verify_stage(A, stage, cnt, lane, S.k, S.metric);
+        if (FUSED) verify_stage(A, stage, cnt, lane, k, metric);
         __syncthreads();
     }
     if (!FUSED) flush_stage(A, stage, cnt, lane);
@@ -671,7 +700,7 @@ __global__ void __launch_bounds__(FM_THREADS, FM_MIN_BLOCKS) k_filter_mma(Filter
         }
         __syncthreads();
         const int nr = (int)((nq + 15u) / 16u);
-        const float Tf = (float)((W == 32 ? 32 : 16) - 4 * S.k);  // pass iff dot >= W - 4k
+        const float Tf = (float)((W == 32 ? 32 : 16) - 4 * S.k * A.tmul);  // pass iff dot >= W - 4 tmul k
         const __half2 hb = __float2half2_rn(0.5f - Tf);
         const uint32_t bias = *reinterpret_cast<const uint32_t *>(&hb);
         uint32_t a[FM_RT][4];
@@ -747,64 +776,70 @@ static int launch_mma(const FilterArgs &A, cudaStream_t st) {
     return FP_OK;
 }
 
-template <int W, int V, bool POS, bool FUSED, bool COMB = false>
+template <int W, int V, int FDK, bool FUSED, bool COMB = false>
 static int launch_one(const FilterArgs &A, bool k1mix, cudaStream_t st) {
+    constexpr bool MIX = W == 32 && FDK == FDK_POPC;  // the k = 1 mixed POPC / ALU test needs popcount fingerprints
     static int grid[2] = {0, 0};
     int &g = grid[k1mix ? 1 : 0];
     if (g == 0) {
         int per_sm = 0;
         if (k1mix)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_tiled<W, V, POS, (W == 32 && !POS), FUSED, COMB>,
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_tiled<W, V, FDK, MIX, FUSED, COMB>,
                                                           FT_THREADS, 0);
         else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_tiled<W, V, POS, false, FUSED, COMB>, FT_THREADS,
-                                                          0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_tiled<W, V, FDK, false, FUSED, COMB>,
+                                                          FT_THREADS, 0);
         g = sm_count() * (per_sm > 0 ? per_sm : 1);
     }
-    if (k1mix) k_filter_tiled<W, V, POS, (W == 32 && !POS), FUSED, COMB><<<g, FT_THREADS, 0, st>>>(A);
-    else k_filter_tiled<W, V, POS, false, FUSED, COMB><<<g, FT_THREADS, 0, st>>>(A);
+    if (k1mix) k_filter_tiled<W, V, FDK, MIX, FUSED, COMB><<<g, FT_THREADS, 0, st>>>(A);
+    else k_filter_tiled<W, V, FDK, false, FUSED, COMB><<<g, FT_THREADS, 0, st>>>(A);
     FP_LAUNCHED(FUSED ? "k_filter_tiled(fused)" : "k_filter_tiled");
     return FP_OK;
 }
 
+// The F_D kind of a fingerprint type.
+static int fd_kind(int type) { return type == FP_POS ? FDK_POS : (type == FP_COUNT_L1 ? FDK_L1 : FDK_POPC); }
+
 template <bool FUSED>
 static int dispatch(const FilterArgs &A, const FpParams &fp, const FilterCfg &cfg, cudaStream_t st) {
-    const bool pos = fp.type == FP_POS;
+    const int kind = fd_kind(fp.type);
+    const bool pos = kind == FDK_POS;
     // combined types (32-bit count fingerprints only): their own instances, so
     // that the other kernels carry no second check
-    const bool comb = A.qfp2 != nullptr && fp.width == 32 && !pos;
-    const bool mix0 = cfg.k1mix && fp.width == 32 && !pos;
+    const bool comb = A.qfp2 != nullptr && fp.width == 32 && kind == FDK_POPC;
+    const bool mix = cfg.k1mix && fp.width == 32 && kind == FDK_POPC;
     if (comb) {
         if (cfg.mma) return launch_mma<32, FUSED, true>(A, st);
-        return launch_one<32, 4, false, FUSED, true>(A, mix0, st);
+        return launch_one<32, 4, FDK_POPC, FUSED, true>(A, mix, st);
     }
+    if (kind == FDK_L1)  // count L1: 4 words per thread, no mixed test, no tensor-core form
+        return fp.width == 32 ? launch_one<32, 4, FDK_L1, FUSED>(A, false, st)
+                              : launch_one<16, 4, FDK_L1, FUSED>(A, false, st);
     if (cfg.mma && !pos) return fp.width == 32 ? launch_mma<32, FUSED, false>(A, st) : launch_mma<16, FUSED, false>(A, st);
-    // the mixed POPC / ALU test applies to 32-bit popcount-type fingerprints at k = 1
-    const bool mix = cfg.k1mix && fp.width == 32 && !pos;
     if (FUSED) {  // the fused form is built for 4 words per thread only
         if (fp.width == 32)
-            return pos ? launch_one<32, 4, true, true>(A, false, st) : launch_one<32, 4, false, true>(A, mix, st);
-        return pos ? launch_one<16, 4, true, true>(A, false, st) : launch_one<16, 4, false, true>(A, false, st);
+            return pos ? launch_one<32, 4, FDK_POS, true>(A, false, st) : launch_one<32, 4, FDK_POPC, true>(A, mix, st);
+        return pos ? launch_one<16, 4, FDK_POS, true>(A, false, st) : launch_one<16, 4, FDK_POPC, true>(A, false, st);
     }
     if (fp.width == 32) {
         if (cfg.v == 4)
-            return pos ? launch_one<32, 4, true, false>(A, false, st) : launch_one<32, 4, false, false>(A, mix, st);
-        return pos ? launch_one<32, 8, true, false>(A, false, st) : launch_one<32, 8, false, false>(A, mix, st);
+            return pos ? launch_one<32, 4, FDK_POS, false>(A, false, st) : launch_one<32, 4, FDK_POPC, false>(A, mix, st);
+        return pos ? launch_one<32, 8, FDK_POS, false>(A, false, st) : launch_one<32, 8, FDK_POPC, false>(A, mix, st);
     }
     if (cfg.v == 4)
-        return pos ? launch_one<16, 4, true, false>(A, false, st) : launch_one<16, 4, false, false>(A, false, st);
-    return pos ? launch_one<16, 8, true, false>(A, false, st) : launch_one<16, 8, false, false>(A, false, st);
+        return pos ? launch_one<16, 4, FDK_POS, false>(A, false, st) : launch_one<16, 4, FDK_POPC, false>(A, false, st);
+    return pos ? launch_one<16, 8, FDK_POS, false>(A, false, st) : launch_one<16, 8, FDK_POPC, false>(A, false, st);
 }
 
-int tile_words(int width, int v) { return (width == 32 ? v : 2 * v) * FT_THREADS; }
+int tile_words(int width, int v) { return (width == 32 ? v : 2 * v) * FT_THREADS * FT_COLS; }
 
 void tile_shape(const FilterCfg &cfg, const FpParams &fp, int *tq, int *tw) {
-    if (cfg.mma && fp.type != FP_POS) {
+    if (cfg.mma && fd_kind(fp.type) == FDK_POPC) {
         *tq = FM_TQ;
         *tw = FM_TW;
     } else {
         *tq = cfg.tq < 1 ? 1 : (cfg.tq > FT_MAX_TQ ? FT_MAX_TQ : cfg.tq);
-        *tw = tile_words(fp.width, cfg.v);
+        *tw = tile_words(fp.width, fd_kind(fp.type) == FDK_L1 ? 4 : cfg.v);
     }
 }
 
@@ -821,6 +856,7 @@ static FilterArgs make_args(const Bucketed &q, const Bucketed &d, const QueryPla
     A.M.high = fp.pos_high | (rep ? fp.pos_high << 16 : 0u);
     A.M.occ = fp.pos_occ | (rep ? fp.pos_occ << 16 : 0u);
     A.tq = cfg.tq < 1 ? 1 : (cfg.tq > FT_MAX_TQ ? FT_MAX_TQ : cfg.tq);
+    A.tmul = fp.q > 0 ? fp.q : 1;
     A.qfp2 = q.fp2;  // combined types (null otherwise); both sets or neither
     A.dfp2 = q.fp2 ? d.fp2 : nullptr;
     return A;

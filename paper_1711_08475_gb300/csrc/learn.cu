@@ -392,6 +392,8 @@ int fp_sample_pairs(fp_index *ix, const uint8_t *chars, const int64_t *offsets, 
         return fail(FP_E_INVAL, "fp_sample_pairs: bad argument");
     if (metric == FP_LEV && (ix->P.type == FP_OCC_HALVED || ix->P.type == FP_POS))
         return fail(FP_E_UNSUPPORTED, "occurrence-halved and position fingerprints bound only the Hamming distance");
+    if (ix->P.type == FP_QGRAM || ix->P.type == FP_COUNT_L1)
+        return fail(FP_E_UNSUPPORTED, "pair sampling: symbol fingerprints compared by their Hamming weight only");
     cudaStream_t st = (cudaStream_t)cuda_stream;
     int64_t total = 0;
     int64_t *d_off = nullptr;
@@ -521,7 +523,10 @@ int fp_learn_map(int fields, const uint64_t *masks, const uint8_t *match, int64_
     };
     for (int i = 0; i < HID * NSYM; i++) h[P_W1 + i] = uni() * 1.0f;  // fan_in 1 (one-hot input)
     for (int i = 0; i < MAXF * HID; i++) h[P_W2 + i] = uni() * (1.0f / sqrtf((float)HID));
-    FP_CUDA(cudaMemcpyAsync(w.prm, h.data(), 4 * NPARAM, cudaMemcpyHostToDevice, st));
+    if (o.init_params)  // the caller's starting point instead (host or device)
+        FP_CUDA(cudaMemcpyAsync(w.prm, o.init_params, 4 * NPARAM, cudaMemcpyDefault, st));
+    else
+        FP_CUDA(cudaMemcpyAsync(w.prm, h.data(), 4 * NPARAM, cudaMemcpyHostToDevice, st));
     FP_CUDA(cudaMemsetAsync(w.m1, 0, 4 * NPARAM, st));
     FP_CUDA(cudaMemsetAsync(w.m2, 0, 4 * NPARAM, st));
     int rc = FP_OK;

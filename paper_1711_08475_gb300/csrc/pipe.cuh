@@ -34,6 +34,7 @@ struct Pipe {
     int32_t *d_group_km = nullptr;     // [2 * MAX_GROUPS]: k of each group, then its metric
     int32_t *d_group = nullptr;        // [queries]
     Bucketed Q;
+    uint32_t *q_fp2 = nullptr;  // second fingerprints of the patterns (combined-type indexes)
     BucketScratch S{};
     QueryPlan qp;
     int32_t seg_cap = 0;  // segments the arena holds

@@ -69,7 +69,8 @@ size_t pipe_layout(const PipeShape &s, uint8_t *base, Pipe *p) {
     const size_t o_chars = carve(off, (size_t)s.chars + 16), o_off = carve(off, 8 * (size_t)(n + 1)),
                  o_bs = carve(off, 8 * (size_t)(s.batches + 1)), o_bg = carve(off, 4 * (size_t)s.batches),
                  o_km = carve(off, 4 * 2 * MAX_GROUPS), o_grp = carve(off, 4 * (size_t)n),
-                 o_qfp = carve(off, 4 * (size_t)(slots + FP_SLACK_SLOTS)), o_qidx = carve(off, 4 * (size_t)slots),
+                 o_qfp = carve(off, 4 * (size_t)(slots + FP_SLACK_SLOTS)), o_qfp2 = carve(off, 4 * (size_t)slots),
+                 o_qidx = carve(off, 4 * (size_t)slots),
                  o_qlen = carve(off, (size_t)slots), o_qrow = carve(off, 4 * (size_t)slots),
                  o_qstr = carve(off, (size_t)strb), o_bst = carve(off, 4 * (size_t)nbins),
                  o_bct = carve(off, 4 * (size_t)nbins), o_k1 = carve(off, 8 * (size_t)n),
@@ -89,6 +90,7 @@ size_t pipe_layout(const PipeShape &s, uint8_t *base, Pipe *p) {
         p->d_group = (int32_t *)(base + o_grp);
         p->Q = Bucketed{};
         p->Q.fp = base + o_qfp;
+        p->q_fp2 = (uint32_t *)(base + o_qfp2);
         p->Q.idx = (int32_t *)(base + o_qidx);
         p->Q.len = base + o_qlen;
         p->Q.row16 = (uint32_t *)(base + o_qrow);
@@ -156,11 +158,15 @@ int pipe_enqueue(fp_index *ix, const FilterCfg &cfg, Pipe &p, int64_t n, int64_t
     const bool band = ix->d_wstart != nullptr;
     FP_TRY(bucketize_into(p.d_chars, p.d_off, n, total, p.d_group, n_groups, ix->d_map, ix->P, st, &p.Q, p.S,
                           p.d_err, band));
+    // combined types (f3): the patterns' second fingerprints, so that the fused
+    // kernel keeps a pair only if both fingerprints pass
+    p.Q.fp2 = ix->d_map2 ? p.q_fp2 : nullptr;
+    if (ix->d_map2) FP_TRY(second_fingerprints(&p.Q, ix->d_map2, ix->P2, st));
     p.qp.max_segments = p.seg_cap;
     int tq = 0, tw = 0;
     tile_shape(cfg, ix->P, &tq, &tw);
     FP_TRY(plan_segments(p.Q, ix->D, p.d_group_km, p.d_group_km + MAX_GROUPS, tq, tw, &p.qp, st,
-                         band ? ix->d_wstart : nullptr, ix->P.width));
+                         band ? ix->d_wstart : nullptr, ix->P.width, ix->P.q));
     if (ev) FP_CUDA(cudaEventRecord(ev[1], st));
     FP_TRY(launch_fused(p.Q, ix->D, p.qp, ix->P, cfg, ix->idx_bits, p.matches, p.match_cap, st, nullptr));
     if (ev) FP_CUDA(cudaEventRecord(ev[2], st));
@@ -199,6 +205,9 @@ int fp_plan_create(fp_index *ix, int64_t max_queries, int64_t max_chars, int32_t
     init_pool();
     fp_query_opts o{};
     if (opts) o = *opts;
+    if (o.mode != FP_MODE_TILED && o.mode != FP_MODE_FUSED)
+        return fail(FP_E_UNSUPPORTED, "fp_plan_create: plans run the fused pipeline (mode TILED or FUSED)");
+    if (o.flags & ~FP_OPT_NO_GRAPH) return fail(FP_E_INVAL, "fp_plan_create: unknown flags");
     fp_plan *p = new fp_plan();
     p->ix = ix;
     p->cap.queries = max_queries;
@@ -210,7 +219,7 @@ int fp_plan_create(fp_index *ix, int64_t max_queries, int64_t max_chars, int32_t
     p->cfg.tq = o.tile_queries > 0 ? std::min(o.tile_queries, 256) : 256;
     p->cfg.k1mix = o.variant == 0;  // the kernel takes the mixed test only in k = 1 tiles
     p->cfg.mma = o.variant == 2;
-    p->use_graph = o.mode != FP_MODE_PLAIN;  // FP_MODE_PLAIN here means: run the pipeline without a graph
+    p->use_graph = !(o.flags & FP_OPT_NO_GRAPH);
     int rc = FP_OK;
     if (cudaStreamCreateWithFlags(&p->st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming) != cudaSuccess ||
@@ -422,7 +431,8 @@ int fp_query_batched(fp_index *ix, const uint8_t *chars, const int64_t *offsets,
     }
     fp_query_opts o{};
     if (opts) o = *opts;
-    o.mode = FP_MODE_PLAIN;  // one-off: no graph
+    o.mode = FP_MODE_FUSED;
+    o.flags |= FP_OPT_NO_GRAPH;  // one-off: no graph
     fp_plan *p = nullptr;
     FP_TRY(fp_plan_create(ix, std::max<int64_t>(n_queries, 1), total, n_batches, &o, &p));
     int rc = fp_plan_run(p, chars, offsets, n_queries, batches, n_batches, cuda_stream, out);

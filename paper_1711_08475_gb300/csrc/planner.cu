@@ -82,7 +82,7 @@ template <bool WRITE>
 __device__ void plan_unit(int c, int64_t u, const int32_t *__restrict__ qb_start, const int32_t *__restrict__ qb_count,
                           const int32_t *__restrict__ db_start, const int32_t *__restrict__ db_count,
                           const int32_t *__restrict__ group_k, const int32_t *__restrict__ group_metric, int tq,
-                          int tw, const void *q_fp, int width, const int32_t *__restrict__ d_wstart, bool band,
+                          int tw, const void *q_fp, int width, int tmul, const int32_t *__restrict__ d_wstart, bool band,
                           Segment *seg, int max_segments, int64_t &si, uint64_t &tb, PlanCounts &pc) {
     const int qc = qb_count[c];
     const int g = c >> 8, n = c & 255, k = group_k[g], metric = group_metric[g];
@@ -102,7 +102,7 @@ __device__ void plan_unit(int c, int64_t u, const int32_t *__restrict__ qb_start
         return;
     }
     const int R1 = cell_part_radix(width, 1), R2 = cell_part_radix(width, 2), NC = cell_count(width);
-    const int H0 = cell_part_bits(width, 0), H1 = R1 - 1, H2 = R2 - 1, r2k = 2 * k;
+    const int H0 = cell_part_bits(width, 0), H1 = R1 - 1, H2 = R2 - 1, r2k = 2 * k * tmul;  // F_D <= 2 tmul k can pass
     const int cf = slot_cell_of(q_fp, width, q0), cl = slot_cell_of(q_fp, width, q0 + (uint32_t)qn - 1u);
     // the tile's box from its first and last pattern (cell order is
     // lexicographic in (x, y, z))
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(1024) k_plan_segments(
     const int32_t *__restrict__ qb_start, const int32_t *__restrict__ qb_count, int q_nbins,
     const int32_t *__restrict__ db_start, const int32_t *__restrict__ db_count,
     const int32_t *__restrict__ group_k, const int32_t *__restrict__ group_metric, int tq, int tw, const void *q_fp,
-    int width, const int32_t *__restrict__ d_wstart, Segment *__restrict__ seg, int max_segments,
+    int width, int tmul, const int32_t *__restrict__ d_wstart, Segment *__restrict__ seg, int max_segments,
     uint64_t *__restrict__ scal, const uint64_t *only_if) {
     if (only_if && *only_if == 0) return;  // block-uniform
     __shared__ int32_t s_unit0[PLAN_MAX_BINS + 1];  // first unit of every bin
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(1024) k_plan_segments(
         for (int64_t u = u0, c = c0; u < u1; u++) {
             while (s_unit0[c + 1] <= u) c++;
             plan_unit<false>((int)c, u - s_unit0[c], qb_start, qb_count, db_start, db_count, group_k, group_metric,
-                             tq, tw, q_fp, width, d_wstart, band, seg, max_segments, si, tb, pc);
+                             tq, tw, q_fp, width, tmul, d_wstart, band, seg, max_segments, si, tb, pc);
         }
         s_n[t] = pc.nseg;
         s_t[t] = pc.tiles;
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(1024) k_plan_segments(
     for (int64_t u = u0, c = c0; u < u1; u++) {
         while (s_unit0[c + 1] <= u) c++;
         plan_unit<true>((int)c, u - s_unit0[c], qb_start, qb_count, db_start, db_count, group_k, group_metric, tq,
-                        tw, q_fp, width, d_wstart, band, seg, max_segments, si, tb, again);
+                        tw, q_fp, width, tmul, d_wstart, band, seg, max_segments, si, tb, again);
     }
     if (t == 1023) {
         const int64_t ns = s_n[1023];
@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(128) k_plan_units(
     const int32_t *__restrict__ qb_start, const int32_t *__restrict__ qb_count, int nbins,
     const int32_t *__restrict__ db_start, const int32_t *__restrict__ db_count,
     const int32_t *__restrict__ group_k, const int32_t *__restrict__ group_metric, int tq, int tw, const void *q_fp,
-    int width, const int32_t *__restrict__ d_wstart, Segment *__restrict__ seg, int max_segments,
+    int width, int tmul, const int32_t *__restrict__ d_wstart, Segment *__restrict__ seg, int max_segments,
     const int32_t *__restrict__ unit0, int32_t *__restrict__ u_seg, uint64_t *__restrict__ u_tiles,
     uint64_t *__restrict__ acc) {
     __shared__ unsigned long long s_sum[2];
@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(128) k_plan_units(
         int64_t si = WRITE ? (int64_t)u_seg[u] : 0;
         uint64_t tb = WRITE ? u_tiles[u] : 0;
         plan_unit<WRITE>(lo, u - unit0[lo], qb_start, qb_count, db_start, db_count, group_k, group_metric, tq, tw,
-                         q_fp, width, d_wstart, true, seg, max_segments, si, tb, pc);
+                         q_fp, width, tmul, d_wstart, true, seg, max_segments, si, tb, pc);
         if (!WRITE) {
             u_seg[u] = pc.nseg;
             u_tiles[u] = pc.tiles;
@@ -440,33 +440,33 @@ void plan_scratch_place(QueryPlan *plan, uint8_t *base, int64_t units_cap, int n
 
 int plan_segments(const Bucketed &q, const Bucketed &d, const int32_t *d_group_k,
                   const int32_t *d_group_metric, int tq, int tw, QueryPlan *plan, cudaStream_t st,
-                  const int32_t *d_wstart, int width) {
+                  const int32_t *d_wstart, int width, int tmul) {
     if (d_wstart && plan->unit0 && plan->units_cap > 0) {
         const unsigned blocks = (unsigned)((plan->units_cap + 127) / 128);
         k_plan_prefix<<<1, 1024, 0, st>>>(q.b_count, q.nbins, tq, plan->unit0, plan->acc, plan->units_cap);
         FP_LAUNCHED("k_plan_prefix");
         k_plan_units<false><<<blocks, 128, 0, st>>>(q.b_start, q.b_count, q.nbins, d.b_start, d.b_count, d_group_k,
-                                                    d_group_metric, tq, tw, q.fp, width, d_wstart, plan->seg,
+                                                    d_group_metric, tq, tw, q.fp, width, tmul, d_wstart, plan->seg,
                                                     plan->max_segments, plan->unit0, plan->u_seg, plan->u_tiles,
                                                     plan->acc);
         FP_LAUNCHED("k_plan_units");
         k_plan_offsets<<<1, 1024, 0, st>>>(plan->u_seg, plan->u_tiles, plan->acc, plan->max_segments, plan->scal);
         FP_LAUNCHED("k_plan_offsets");
         k_plan_units<true><<<blocks, 128, 0, st>>>(q.b_start, q.b_count, q.nbins, d.b_start, d.b_count, d_group_k,
-                                                   d_group_metric, tq, tw, q.fp, width, d_wstart, plan->seg,
+                                                   d_group_metric, tq, tw, q.fp, width, tmul, d_wstart, plan->seg,
                                                    plan->max_segments, plan->unit0, plan->u_seg, plan->u_tiles,
                                                    plan->acc);
         FP_LAUNCHED("k_plan_units");
         // whole buckets, only when the banded plan did not fit
         k_plan_segments<<<1, 1024, 0, st>>>(q.b_start, q.b_count, q.nbins, d.b_start, d.b_count, d_group_k,
-                                            d_group_metric, tq, tw, nullptr, width, nullptr, plan->seg,
+                                            d_group_metric, tq, tw, nullptr, width, tmul, nullptr, plan->seg,
                                             plan->max_segments, plan->scal, plan->acc + 2);
         FP_LAUNCHED("k_plan_segments");
         return FP_OK;
     }
     k_plan_segments<<<1, 1024, 0, st>>>(q.b_start, q.b_count, q.nbins, d.b_start, d.b_count, d_group_k,
-                                        d_group_metric, tq, tw, d_wstart ? q.fp : nullptr, width, d_wstart, plan->seg,
-                                        plan->max_segments, plan->scal, nullptr);
+                                        d_group_metric, tq, tw, d_wstart ? q.fp : nullptr, width, tmul, d_wstart,
+                                        plan->seg, plan->max_segments, plan->scal, nullptr);
     FP_LAUNCHED("k_plan_segments");
     return FP_OK;
 }

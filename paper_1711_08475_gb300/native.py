@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfpmatch.so")
 
 FP_OK, FP_E_INVAL, FP_E_UNSUPPORTED, FP_E_NOMEM, FP_E_CUDA, FP_E_TIMEOUT, FP_E_OVERFLOW = 0, -1, -2, -3, -4, -5, -6
-FP_OCC, FP_OCC_HALVED, FP_COUNT, FP_POS = 0, 1, 2, 3
+FP_OCC, FP_OCC_HALVED, FP_COUNT, FP_POS, FP_QGRAM, FP_COUNT_L1 = 0, 1, 2, 3, 4, 5
 FP_HAM, FP_LEV = 0, 1
 FP_SET_COMMON, FP_SET_RARE, FP_SET_MIXED, FP_SET_CUSTOM = 0, 1, 2, 3
 FP_MODE_TILED, FP_MODE_PLAIN, FP_MODE_FUSED = 0, 1, 2
@@ -21,18 +21,23 @@ FP_MODE_TILED, FP_MODE_PLAIN, FP_MODE_FUSED = 0, 1, 2
 
 class fp_build_opts(ctypes.Structure):
     _fields_ = [("set", ctypes.c_int32), ("count_bits", ctypes.c_int32), ("pos_bits", ctypes.c_int32),
-                ("combined", ctypes.c_int32), ("custom_map", ctypes.POINTER(ctypes.c_int8))]
+                ("combined", ctypes.c_int32), ("custom_map", ctypes.POINTER(ctypes.c_int8)),
+                ("qgram", ctypes.c_int32)]
 
 
 class fp_query_opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("tile_queries", ctypes.c_int32),
-                ("words_per_thread", ctypes.c_int32), ("variant", ctypes.c_int32)]
+                ("words_per_thread", ctypes.c_int32), ("variant", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+FP_OPT_NO_GRAPH = 1
 
 
 class fp_learn_opts(ctypes.Structure):
     _fields_ = [("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
                 ("tau0", ctypes.c_float), ("tau1", ctypes.c_float), ("beta", ctypes.c_float),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64),
+                ("init_params", ctypes.POINTER(ctypes.c_float))]
 
 
 class fp_tune_result(ctypes.Structure):
@@ -61,7 +66,7 @@ class fp_index_info(ctypes.Structure):
     _fields_ = [("n_words", ctypes.c_int64), ("type", ctypes.c_int32), ("width_bits", ctypes.c_int32),
                 ("count_bits", ctypes.c_int32), ("pos_bits", ctypes.c_int32), ("n_pos", ctypes.c_int32),
                 ("sigma", ctypes.c_int32), ("bucket_count", ctypes.c_int64 * 256),
-                ("device_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("qgram", ctypes.c_int32)]
 
 
 class fp_probe_result(ctypes.Structure):
@@ -128,6 +133,7 @@ SIGNATURES = {
     "fp_result_free": (None, [_VP]),
     "fp_index_info_get": (ctypes.c_int, [_VP, ctypes.POINTER(fp_index_info)]),
     "fp_index_map": (ctypes.c_int, [_VP, _VP]),
+    "fp_index_qgrams": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "fp_set_symbol_map": (ctypes.c_int, [_VP, _VP]),
     "fp_fingerprint": (ctypes.c_int, [_VP, _VP, _VP, _I64, _VP, _VP]),
     "fp_free": (None, [_VP]),

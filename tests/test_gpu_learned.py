@@ -46,6 +46,41 @@ def test_gpu_gradients_match_fp64(fp, fields, tau, k):
     assert err <= 1e-4, err
 
 
+def test_gpu_adam_steps_match_fp64(fp):
+    """Two epochs of one full batch each are two Adam steps (beta1 0.9, beta2
+    0.999, eps 1e-8, bias-corrected; tau0 in the first epoch, tau1 in the
+    second).  From the same starting parameters, the library's result must
+    equal the same two steps taken in fp64 on the fp64 reference gradients.
+    Adam divides each update by the gradient's magnitude, so a component is
+    compared tightly only where both steps' gradients are well above the
+    FP32 summation noise (relative 1e-3 of the largest); the rest may differ by
+    the few step sizes Adam's normalisation allows, and rows of fields past
+    `fields` (zero gradient) must not move at all."""
+    fields, k, beta, lr, tau0, tau1 = 24, 1, 2.0, 3e-3, 1.0, 0.5
+    p0 = ((datagen.uniform(datagen.stream_key(5, "adam/p"), learned.NPARAM) * 2 - 1) * 0.4).astype(np.float32)
+    masks, match = sample_set(31, 600)
+    _, p_gpu, _ = fp.fp_learn_map(fields, masks, match, k=k, epochs=2, batch=600, lr=lr, tau0=tau0, tau1=tau1,
+                                  beta=beta, init_params=p0)
+    p = p0.astype(np.float64)
+    m1 = np.zeros_like(p)
+    m2 = np.zeros_like(p)
+    firm = np.ones(p.size, dtype=bool)
+    for step, tau in ((1, tau0), (2, tau1)):
+        _, _, g = learned.loss_and_grad(p, fields, tau, beta, k, masks, match)
+        firm &= np.abs(g) > 1e-3 * np.abs(g).max()
+        m1 = 0.9 * m1 + 0.1 * g
+        m2 = 0.999 * m2 + 0.001 * g * g
+        p = p - lr * (m1 / (1 - 0.9 ** step)) / (np.sqrt(m2 / (1 - 0.999 ** step)) + 1e-8)
+    d_gpu, d_ref = p_gpu.astype(np.float64) - p0, p - p0
+    assert firm.mean() > 0.2, firm.mean()
+    assert np.abs(d_gpu - d_ref)[firm].max() <= 1e-3 * lr
+    assert np.abs(d_gpu - d_ref).max() <= 4 * lr
+    W2, b2 = learned.unpack(p_gpu.astype(np.float64))[2:4]
+    W2_0, b2_0 = learned.unpack(p0.astype(np.float64))[2:4]
+    assert np.array_equal(W2[fields:], W2_0[fields:]) and np.array_equal(b2[fields:], b2_0[fields:])
+    assert np.abs(d_gpu).max() > 0.5 * lr  # the parameters did move
+
+
 @pytest.fixture(scope="module")
 def url_small():
     return datagen.url2m(200000, 6000)
