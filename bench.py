@@ -52,7 +52,12 @@ def parse(argv=None):
     ap.add_argument("--profile", action="store_true", help="no CPU leg, no e2e, few steps (for ncu)")
     ap.add_argument("--url-words", type=int, default=5_000_000, help="URL-like dictionary of the learned/serving legs")
     ap.add_argument("--url-queries", type=int, default=20_000)
-    ap.add_argument("--serve-seconds", type=float, default=8.0, help="span of the Poisson arrivals")
+    ap.add_argument("--serve-requests", type=int, default=300, help="requests replayed at every offered load")
+    ap.add_argument("--serve-loads", default="5000,20000,80000,320000,1280000,5120000",
+                    help="offered loads of the serving curve (patterns/s, comma-separated)")
+    ap.add_argument("--forms-reps", type=int, default=20, help="timed runs of each form of the metric's comparison")
+    ap.add_argument("--no-small", action="store_true", help="skip the uniform10k and url2m legs")
+    ap.add_argument("--no-paper-cpu", action="store_true", help="skip the paper-method CPU timing")
     ap.add_argument("--no-url", action="store_true", help="skip the learned-map and serving legs")
     ap.add_argument("--variant", type=int, default=0, help="filter variant (fp_query_opts.variant)")
     ap.add_argument("--batched-words", type=int, default=10_000_000, help="dictionary of the batched leg")
@@ -160,24 +165,93 @@ def max_over_ranks(pg, x: float) -> float:
     return float(t.item())
 
 
-def cpu_baseline(w, n_sample: int):
-    """The brute-force oracle, as it stands, on all host cores, on a bounded sample."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def oracle_rate(w, per: int, threads: int):
+    """Brute-force oracle query answers per second on `per` Ham + `per` Lev
+    patterns (evenly spaced) against the full dictionary."""
     import oracle
-    cores = os.cpu_count() or 1
-    per = max(1, n_sample // 2)
-    t = 0.0
-    n = 0
+    t, n = 0.0, 0
     for metric in ("ham", "lev"):
         Q = w.queries[metric]
         sel = np.arange(0, len(Q), max(1, len(Q) // per))[:per]
         sub = Q.subset(sel)
         t0 = time.perf_counter()
-        oracle.match(w.dictionary, sub, 1, metric, threads=cores)
+        oracle.match(w.dictionary, sub, 1, metric, threads=threads)
         t += time.perf_counter() - t0
         n += len(sub)
-    return {"value": n / t, "unit": "queries/s", "cores": cores, "kind": "oracle",
+    return n / t, n, t
+
+
+def cpu_baseline(w, n_sample: int):
+    """The brute-force oracle, as it stands, on all host cores and on one core,
+    each on a bounded sample."""
+    cores = os.cpu_count() or 1
+    v, n, t = oracle_rate(w, max(1, n_sample // 2), cores)
+    v1, n1, t1 = oracle_rate(w, max(1, n_sample // 2 // max(cores, 1)), 1)
+    return {"value": v, "unit": "queries/s", "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
             "sample": f"{n} queries ({n // 2} Ham + {n // 2} Lev, evenly spaced) against the full dictionary, "
-                      f"brute force on {cores} threads, {t:.1f} s"}
+                      f"brute force on {cores} threads, {t:.1f} s",
+            "single_thread": {"value": v1, "unit": "queries/s", "cores": 1,
+                              "sample": f"{n1} queries ({n1 // 2} Ham + {n1 // 2} Lev), brute force on 1 thread, "
+                                        f"{t1:.1f} s"}}
+
+
+def paper_method_cpu(cases, per: int = 60):
+    """The paper's own method on one host core (Sec. 4: the pattern's fingerprint
+    built once, Eq. 1 against every eligible word's fingerprint, survivors
+    verified by the early-exit loops) against brute force on one core, on the
+    same sampled patterns: the measured filter-over-brute-force speed-ups, set
+    beside the paper's (over 2.5x for Hamming and over 10x for Levenshtein at
+    k = 1, on one 4.2 GHz i7-6700K thread, Sec. 4.1; context only)."""
+    import oracle
+    out = {}
+    for name, w in cases:
+        res = {}
+        fps = {}
+        for metric in ("ham", "lev"):
+            Q = w.queries[metric]
+            sub = Q.subset(np.arange(0, len(Q), max(1, len(Q) // per))[:per])
+            t0 = time.perf_counter()
+            rp0, idx0 = oracle.match(w.dictionary, sub, 1, metric, threads=1)
+            t_brute = time.perf_counter() - t0
+            row = {"patterns": len(sub), "brute_force_s": t_brute, "pairs": oracle.eligible_pairs(w.dictionary, sub, 1,
+                                                                                                   metric)}
+            for t, width in (("occ", 16), ("count", 16)):
+                m, _, _ = oracle.symbol_map(w.dictionary.chars, "common", oracle.layout(t, width)["sigma"])
+                dfp = fps.setdefault((t, width), oracle.fingerprints(w.dictionary, m, t, width))  # built beforehand
+                t0 = time.perf_counter()
+                qfp = oracle.fingerprints(sub, m, t, width)  # once per pattern (Sec. 4)
+                rp, idx, pairs, surv = oracle.filter_match_fps(w.dictionary, sub, 1, metric, dfp, qfp, "weight",
+                                                               width, threads=1)
+                t_f = time.perf_counter() - t0
+                assert np.array_equal(rp, rp0) and np.array_equal(idx, idx0)
+                row[f"{t}{width}"] = {"filter_s": t_f, "speedup": t_brute / t_f,
+                                      "rejection_rate": 1.0 - surv / max(pairs, 1)}
+            res[metric] = row
+        out[name] = res
+    return {"what": "the paper's method (fingerprint once, Eq. 1, early-exit verify; oracle.c) vs brute force, "
+                    "both on 1 host thread, same patterns, identical match lists; the dictionary's fingerprints "
+                    "built beforehand (Sec. 3.4 preprocessing, outside the method's time), the patterns' inside",
+            "cpu_model": cpu_model(), "paper_claims": {"ham": ">2.5x", "lev": ">10x", "hardware": "i7-6700K 4.2 GHz"},
+            "workloads": out}
 
 
 def run_reference(args, w, rank, pg):
@@ -290,6 +364,115 @@ def combined_leg(fp, w, ix, dev, metrics, stream, flush, step_device, args):
             "timing": f"mean of {reps} steps, L2 flushed before each, CUDA events"}
 
 
+def fused_leg(fp, ix, dev, metrics, stream, flush, step_device, args):
+    """The headline step in the fused form (filter and verification in one
+    kernel, survivors never leave the SM) against the separate form the
+    headline uses (survivor list in DRAM, then the verification kernel): same
+    patterns, identical match lists."""
+    def step_f():
+        out = []
+        for m in metrics:
+            r = fp.fp_query_ex(ix, dev[m][0], dev[m][1], k=1, metric=m, mode="fused", variant=args.variant)
+            out.append(r.stats())
+            r.free()
+        return out
+
+    reps = max(5, args.steps // 5)
+    ms_f, out_f = timed(step_f, stream, flush, reps)
+    ms_s, _ = timed(step_device, stream, flush, reps)
+    same = True
+    for m in metrics:
+        a = fp.fp_query_ex(ix, dev[m][0], dev[m][1], k=1, metric=m, mode="fused", variant=args.variant)
+        b = fp.fp_query_ex(ix, dev[m][0], dev[m][1], k=1, metric=m, variant=args.variant)
+        same &= same_csr(a.csr(), b.csr())
+        a.free()
+        b.free()
+    return {"fused_ms_per_step": ms_f, "separate_ms_per_step": ms_s,
+            "fused_stage_ms_per_step": {k_: sum(st[k_] for st in out_f) for k_ in ("ms_prepare", "ms_filter",
+                                                                                   "ms_verify", "ms_emit")},
+            "identical": bool(same), "timing": f"mean of {reps} steps, L2 flushed before each, CUDA events"}
+
+
+def scan_leg(fp, torch, w, cases, stream, flush, peak, reps: int = 10):
+    """The tiled filter (weight bands where the type allows) on one workload:
+    per (fingerprint, metric) device-resident query answers per second,
+    eligible pair-compares per second, the rejection rate of the bound, the
+    filter kernel's pair tests per second against the roofline peak, and 16
+    evenly spaced patterns checked against the oracle."""
+    import oracle
+    out = {}
+    cores = os.cpu_count() or 1
+    for case in cases:
+        t, width, metrics = case[:3]
+        opts = case[3] if len(case) > 3 else {}
+        ix = fp.fp_build(w.dictionary, fp_type=t, width=width, **opts)
+        tag = f"{t}{width}" + "".join(f"_{k_}{v}" for k_, v in opts.items())
+        for m in metrics:
+            Q = w.queries[m]
+            dq = (torch.from_numpy(Q.chars).cuda(), torch.from_numpy(Q.offsets).cuda())
+            ms, r = timed(lambda: fp.fp_query_ex(ix, dq[0], dq[1], k=1, metric=m), stream, flush, reps)
+            st = r.stats()
+            rp, idx = r.csr()
+            r.free()
+            pick = np.arange(0, len(Q), max(1, len(Q) // 16))[:16]
+            orp, oidx = oracle.match(w.dictionary, Q.subset(pick), 1, m, threads=cores)
+            ok = all(np.array_equal(idx[rp[i]:rp[i + 1]], oidx[orp[j]:orp[j + 1]]) for j, i in enumerate(pick))
+            tests_per_s = st["pairs_tested"] / (st["ms_filter"] / 1e3) if st["ms_filter"] > 0 else None
+            out[f"{tag}_{m}"] = {
+                "queries_per_s": len(Q) / (ms / 1e3), "ms": ms, "pair_compares_per_s": st["pairs"] / (ms / 1e3),
+                "pairs": st["pairs"], "pairs_tested": st["pairs_tested"], "survivors": st["survivors"],
+                "matches": st["matches"], "rejection_rate": 1.0 - st["survivors"] / max(st["pairs"], 1),
+                "stage_ms": {k_: st[k_] for k_ in ("ms_prepare", "ms_filter", "ms_verify", "ms_emit")},
+                "filter_pair_tests_per_s": tests_per_s,
+                "filter_frac": tests_per_s / peak if tests_per_s else None,
+                "oracle_checked_patterns": int(len(pick)), "oracle_ok": bool(ok)}
+        ix.free()
+    return out
+
+
+def small_legs(fp, torch, args, stream, flush, peak):
+    """The SURVEY's first and third configurations as bench lines: the uniform
+    10,000-word dictionary (occ16) and the 2,000,000-string URL-like one
+    (occ32 for both metrics, pos32 for Hamming), k = 1, full query sets."""
+    import datagen
+    t0 = time.perf_counter()
+    u = datagen.uniform10k()
+    url = datagen.url2m()
+    gen_s = time.perf_counter() - t0
+    return {"uniform10k": {"workload": "10,000 words, lengths U{4..12}, letters uniform a..z; 1,000 patterns per "
+                                       "metric (50% one-edit mutations); k=1",
+                           "legs": scan_leg(fp, torch, u, [("occ", 16, ("ham", "lev"))], stream, flush, peak)},
+            "url2m": {"workload": "2,000,000 URL-like strings (lognormal lengths median 45, 15..120, 40% shared "
+                                  "prefixes); 100,000 patterns per metric (50% one-edit mutations); k=1",
+                      "legs": scan_leg(fp, torch, url, [("occ", 32, ("ham", "lev")), ("pos", 32, ("ham",)),
+                                                        ("qgram", 32, ("ham", "lev"), {"qgram": 2}),
+                                                        ("qgram", 32, ("ham", "lev"), {"qgram": 3})],
+                                       stream, flush, peak),
+                      "generation_s": gen_s}}, url
+
+
+def count_l1_leg(fp, torch, w, stream, flush, peak):
+    """The headline workload with the count fingerprint in the paper's binary
+    code compared by the L1 distance of the counts (FP_COUNT_L1) beside the
+    Gray-coded count32 of the headline: survivors, step time, filter rate."""
+    return {"workload": WORKLOAD.replace("count32 fingerprint", "count fingerprints"),
+            "legs": scan_leg(fp, torch, w, [("count_l1", 32, ("ham", "lev")), ("count", 32, ("ham", "lev"))], stream,
+                             flush, peak, reps=5)}
+
+
+def e2e_rate(fn, n_patterns: int, reps: int = 5, warm: int = 1):
+    """Patterns per second of fn() (host inputs in, match lists back in host memory), wall clock."""
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        fn()
+    torch.cuda.synchronize()
+    return n_patterns * reps / (time.perf_counter() - t0)
+
+
 def url_legs(fp, torch, args, stream, flush):
     """The learned map and the serving loop on URL-like strings (k = 1, Lev).
 
@@ -297,14 +480,16 @@ def url_legs(fp, torch, args, stream, flush):
     dictionary fingerprint read once per pattern) against the batched form
     (one captured plan: fused filter + verify over all patterns) with the
     frequency map and with the learned map; every form must give the same
-    match lists, and a sample of patterns is checked against the oracle.
-    serving: Poisson arrivals (mean 5,000 patterns/s, requests of 1..4,096
-    patterns) replayed against the serving loop on the learned index, then the
-    same requests as one burst on the learned and on the frequency index."""
+    match lists, and a sample of patterns is checked against the oracle; each
+    form is also timed end to end from pinned host buffers through the C ABI.
+    serving: one stream of Poisson-arrival requests (1..4,096 patterns each)
+    replayed against the serving loop on the learned index at several offered
+    loads (the same requests, arrival times scaled), then as one burst on the
+    learned and on the frequency index; every run must give the same lists."""
     import datagen
     import oracle
     t0 = time.perf_counter()
-    w, reqs = datagen.serving5m(args.url_words, duration_s=args.serve_seconds)
+    w, _ = datagen.serving5m(args.url_words, duration_s=0.001)
     gen_s = time.perf_counter() - t0
     freq = fp.fp_build(w.dictionary, fp_type="occ", width=32)
     # training pairs: the frequency-map filter on patterns of their own (not the measured ones)
@@ -319,130 +504,226 @@ def url_legs(fp, torch, args, stream, flush):
     lrn = fp.fp_build(w.dictionary, fp_type="occ", width=32, custom_map=mp)
     Q = datagen.make_queries(w.dictionary, w.law, w.seed, "bench/lev", args.url_queries, 0.5, "lev")
     dq = (torch.from_numpy(Q.chars).cuda(), torch.from_numpy(Q.offsets).cuda())
+    hq = (torch.from_numpy(Q.chars).pin_memory().numpy(), torch.from_numpy(Q.offsets).pin_memory().numpy())
     nq = len(Q)
     plans = {name: fp.Plan(ix, nq, len(Q.chars), 1) for name, ix in (("freq", freq), ("learned", lrn))}
     batch = [(nq, 1, "lev")]
 
-    def plain():
-        return fp.fp_query_ex(freq, dq[0], dq[1], k=1, metric="lev", mode="plain")
+    def plain(src=dq):
+        return fp.fp_query_ex(freq, src[0], src[1], k=1, metric="lev", mode="plain")
 
-    def batched(name):
-        return lambda: plans[name].run(dq[0], dq[1], batches=batch)
+    def batched(name, src=dq):
+        return lambda: plans[name].run(src[0], src[1], batches=batch)
+
+    def through(fn):  # the result's match lists copied back to host memory
+        def run():
+            r = fn()
+            r.csr(copy=False)
+            r.free()
+        return run
 
     forms = {}
     outs = {}
-    for name, fn, reps in (("plain_gpu_freq", plain, 3), ("batched_freq", batched("freq"), 5),
-                           ("batched_learned", batched("learned"), 5)):
-        ms, r = timed(fn, stream, flush, reps)
+    for name, fn, hfn in (("plain_gpu_freq", plain, lambda: plain(hq)),
+                          ("batched_freq", batched("freq"), batched("freq", hq)),
+                          ("batched_learned", batched("learned"), batched("learned", hq))):
+        ms, r = timed(fn, stream, flush, args.forms_reps)
         st = r.stats()
         outs[name] = r.csr()
         r.free()
         forms[name] = {"queries_per_s": nq / (ms / 1e3), "pair_compares_per_s": st["pairs"] / (ms / 1e3),
-                       "ms": ms, "pairs": st["pairs"], "survivors": st["survivors"], "matches": st["matches"],
-                       "rejection_rate": 1.0 - st["survivors"] / max(st["pairs"], 1)}
+                       "ms": ms, "reps": args.forms_reps, "pairs": st["pairs"], "survivors": st["survivors"],
+                       "matches": st["matches"], "rejection_rate": 1.0 - st["survivors"] / max(st["pairs"], 1),
+                       "e2e": {"value": e2e_rate(through(hfn), nq), "unit": "queries/s",
+                               "h2d_bytes": int(Q.chars.nbytes + Q.offsets.nbytes),
+                               "d2h_bytes": int(outs[name][0].nbytes + outs[name][1].nbytes)}}
     ref = outs["plain_gpu_freq"]
     identical = all(same_csr(ref, o) for o in outs.values())
     pick = np.arange(0, nq, max(1, nq // 48))[:48]
     orp, oidx = oracle.match(w.dictionary, Q.subset(pick), 1, "lev", threads=os.cpu_count() or 1)
     rp, idx = outs["batched_learned"]
     oracle_ok = all(np.array_equal(idx[rp[i]:rp[i + 1]], oidx[orp[j]:orp[j + 1]]) for j, i in enumerate(pick))
-    for p in plans.values():
-        p.free()
+    for p_ in plans.values():
+        p_.free()
+    qps = {k_: v["queries_per_s"] for k_, v in forms.items()}
 
-    # ---- serving loop ----------------------------------------------------
+    # ---- the same at k = 2, where verification weighs more: a map trained at k = 2
+    smp2 = fp.fp_sample_pairs(freq, train_q, k=2, metric="lev", n_samples=2_000_000, seed=12)
+    mp2, _, curve2 = fp.fp_learn_map(32, smp2["masks"], smp2["match"], k=2, seed=4)
+    lrn2 = fp.fp_build(w.dictionary, fp_type="occ", width=32, custom_map=mp2)
+    plans2 = {name: fp.Plan(ix, nq, len(Q.chars), 1) for name, ix in (("freq", freq), ("learned", lrn2))}
+    batch2 = [(nq, 2, "lev")]
+    k2 = {}
+    outs2 = {}
+    for name in ("freq", "learned"):
+        ms, r = timed(lambda: plans2[name].run(dq[0], dq[1], batches=batch2), stream, flush, args.forms_reps)
+        st = r.stats()
+        outs2[name] = r.csr()
+        r.free()
+        k2[f"batched_{name}"] = {"queries_per_s": nq / (ms / 1e3), "ms": ms, "pairs": st["pairs"],
+                                 "survivors": st["survivors"], "matches": st["matches"],
+                                 "rejection_rate": 1.0 - st["survivors"] / max(st["pairs"], 1)}
+    for p_ in plans2.values():
+        p_.free()
+    lrn2.free()
+    pick2 = np.arange(0, nq, max(1, nq // 16))[:16]
+    orp2, oidx2 = oracle.match(w.dictionary, Q.subset(pick2), 2, "lev", threads=os.cpu_count() or 1)
+    rp2, idx2 = outs2["learned"]
+    k2["learned_map_share"] = k2["batched_learned"]["queries_per_s"] / k2["batched_freq"]["queries_per_s"]
+    k2["identical_results"] = same_csr(outs2["freq"], outs2["learned"])
+    k2["oracle_ok"] = all(np.array_equal(idx2[rp2[i]:rp2[i + 1]], oidx2[orp2[j]:orp2[j + 1]])
+                          for j, i in enumerate(pick2))
+    k2["loss_first_last_epoch"] = [float(curve2[0]), float(curve2[-1])]
+
+    # ---- serving loop: one request stream at several offered loads ---------
+    loads = [float(x) for x in args.serve_loads.split(",") if x]
+    reqs, _ = datagen.poisson_requests(w.dictionary, w.law, w.seed, 0.0, loads[0], label="serve",
+                                       n_requests=args.serve_requests)
     allq = datagen.Strings.concat([r.queries for r in reqs])
     sizes = np.array([len(r.queries) for r in reqs], np.int64)
-    arrive = np.array([int(r.arrival_s * 1e6) for r in reqs], np.int64)
-    srv = fp.Server(lrn, lanes=4)
-    t0 = time.perf_counter()
-    res, lat = srv.replay(allq, request_sizes=sizes, arrival_us=arrive, k=1, metric="lev")
-    wall = time.perf_counter() - t0
-    st = srv.stats()
-    srv.free()
-    served = res.csr()
-    res.free()
+    t_at_first = np.array([r.arrival_s for r in reqs])  # arrival times at the first offered load
+    curve_pts = []
+    first = None
+    identical_all = True
+    for load in loads:
+        arrive = (t_at_first * (loads[0] / load) * 1e6).astype(np.int64)
+        srv = fp.Server(lrn, lanes=4)
+        t0 = time.perf_counter()
+        res, lat = srv.replay(allq, request_sizes=sizes, arrival_us=arrive, k=1, metric="lev")
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.free()
+        got = res.csr()
+        res.free()
+        if first is None:
+            first = got
+        same_ = same_csr(first, got)
+        identical_all &= same_
+        curve_pts.append({"offered_queries_per_s": len(allq) / (arrive[-1] / 1e6) if arrive[-1] > 0 else None,
+                          "nominal_load_queries_per_s": load, "requests": int(len(sizes)),
+                          "achieved_queries_per_s": len(allq) / wall, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                          "mean_ms": st["mean_ms"], "max_ms": st["max_ms"], "mean_queue_ms": st["mean_queue_ms"],
+                          "launches": st["launches"], "max_lanes_busy": st["max_lanes_busy"],
+                          "max_requests_per_launch": st["max_requests_per_launch"], "peak_bytes": st["peak_bytes"],
+                          "identical_to_first_load": bool(same_)})
     burst = {}
     for name, ix in (("learned", lrn), ("freq", freq)):
         srv = fp.Server(ix, lanes=4)
         t0 = time.perf_counter()
-        r, blat = srv.replay(allq, request_sizes=sizes, arrival_us=np.zeros_like(arrive), k=1, metric="lev")
+        r, blat = srv.replay(allq, request_sizes=sizes, arrival_us=np.zeros_like(sizes), k=1, metric="lev")
         bw = time.perf_counter() - t0
         bst = srv.stats()
         srv.free()
         burst[name] = {"queries_per_s": len(allq) / bw, "p50_ms": bst["p50_ms"], "p99_ms": bst["p99_ms"],
                        "launches": bst["launches"], "max_requests_per_launch": bst["max_requests_per_launch"],
+                       "max_lanes_busy": bst["max_lanes_busy"],
                        "rejection_rate": 1.0 - bst["survivors"] / max(bst["pairs"], 1),
-                       "identical_to_offered_run": same_csr(r.csr(), served)}
+                       "identical_to_offered_run": same_csr(r.csr(), first)}
         r.free()
     return {
         "forms": {"workload": f"{len(w.dictionary):,} URL-like strings (lognormal lengths median 45, 15..120, 40% "
                               f"shared prefixes), {nq:,} Lev patterns (50% one-edit mutations), k=1, occ32",
+                  "metric_config": "the SURVEY's fifth configuration (learned map + serving), 5M URL-like strings",
                   "forms": forms,
-                  "learned_batched_vs_plain_gpu": forms["batched_learned"]["queries_per_s"]
-                                                  / forms["plain_gpu_freq"]["queries_per_s"],
+                  "learned_batched_vs_plain_gpu": qps["batched_learned"] / qps["plain_gpu_freq"],
+                  "batching_share": qps["batched_freq"] / qps["plain_gpu_freq"],
+                  "learned_map_share": qps["batched_learned"] / qps["batched_freq"],
+                  "learned_batched_vs_plain_gpu_e2e": forms["batched_learned"]["e2e"]["value"]
+                                                      / forms["plain_gpu_freq"]["e2e"]["value"],
                   "identical_results": identical,
                   "oracle_checked_patterns": int(len(pick)), "oracle_ok": oracle_ok,
+                  "k2_lev": k2,
                   "learned_map": {"samples": 2_000_000, "sample_s": t1 - ts, "train_s": t2 - t1,
                                   "loss_first_epoch": float(curve[0]), "loss_last_epoch": float(curve[-1]),
                                   "fields_used": int(len(set(mp[0x20:0x7F].tolist())))},
                   "generation_s": gen_s},
         "serving": {"workload": f"{len(reqs)} requests ({len(allq):,} Lev patterns, sizes U{{1..4096}}) with "
-                                f"Poisson arrivals, mean 5,000 patterns/s over {args.serve_seconds:g} s, k=1, "
+                                f"Poisson arrivals, replayed at each offered load (arrival times scaled), k=1, "
                                 f"learned occ32 index, 4 lanes",
-                    "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "max_ms": st["max_ms"],
-                    "mean_queue_ms": st["mean_queue_ms"], "offered_queries_per_s": len(allq) / args.serve_seconds,
-                    "achieved_queries_per_s": len(allq) / wall, "launches": st["launches"],
-                    "max_lanes_busy": st["max_lanes_busy"], "peak_bytes": st["peak_bytes"],
-                    "budget_bytes": st["budget_bytes"],
-                    "rejection_rate": 1.0 - st["survivors"] / max(st["pairs"], 1),
-                    "burst": burst},
+                    "curve": curve_pts, "identical_across_loads": bool(identical_all), "burst": burst},
     }
 
 
 def batched_leg(fp, torch, args, stream, flush):
     """Uneven batches across all length buckets in one captured plan.
 
-    10,000,000 English-like words (lengths 2..64, count32); 256 batches with
-    sizes floor(exp(U(0, ln 50,000))), each with its own k in {1, 2} and metric;
-    the tile shape of the plan comes from the autotuner (fused form, on a sample
-    of the k = 1 Levenshtein patterns).  The first run captures the graph, the
-    timed runs replay it; a sample of patterns from every (k, metric) pair is
-    checked against the oracle."""
+    10,000,000 English-like words (lengths 2..64); 256 batches with sizes
+    floor(exp(U(0, ln 50,000))), each with its own k in {1, 2} and metric.
+    The index carries combined types (count32 + occ32 over the 32 most
+    frequent symbols: a pair survives only if both pass Eq. 1); the same plan
+    on count32 alone is timed beside it.  The tile comes from the plan
+    autotuner on a uniform 5 % of every batch (so the sample's pairs spread
+    over the (k, metric) groups as the workload's do).  The first run captures
+    the graph, the timed runs replay it; one more run without the graph gives
+    the per-stage split; e2e runs from pinned host buffers with the match
+    lists copied back; patterns of every (k, metric) pair are checked against
+    the oracle."""
     import datagen
     import oracle
     from paper_1711_08475_gb300 import tune
     t0 = time.perf_counter()
     w, batches = datagen.batched10m(args.batched_words, args.batched_batches)
     gen_s = time.perf_counter() - t0
-    ix = fp.fp_build(w.dictionary, fp_type="count", width=32)
     allq = datagen.Strings.concat([b.queries for b in batches])
     spec = [(len(b.queries), b.k, b.metric) for b in batches]
-    lev1 = [b.queries for b in batches if b.k == 1 and b.metric == "lev"]
-    sample = datagen.Strings.concat(lev1) if lev1 else allq
-    sample = sample.subset(np.arange(min(len(sample), 20000)))
-    opts = tune.tuned_opts(ix, sample, k=1, metric="lev", mode="fused", reps=1)
+    # tuning sample: every 20th pattern of every batch
+    sel, sspec = [], []
+    base = 0
+    for n, k, metric in spec:
+        rows = np.arange(base, base + n, 20)
+        if len(rows):
+            sel.append(rows)
+            sspec.append((len(rows), k, metric))
+        base += n
+    sample = allq.subset(np.concatenate(sel))
     dq = (torch.from_numpy(allq.chars).cuda(), torch.from_numpy(allq.offsets).cuda())
-    plan = fp.Plan(ix, len(allq), len(allq.chars), len(spec), tile_queries=opts["tile_queries"],
-                   variant=opts["variant"])
-    ms, r = timed(lambda: plan.run(dq[0], dq[1], batches=spec), stream, flush, reps=2, warm=1)
-    st = r.stats()
-    rp, idx = r.csr()
-    r.free()
-    plan.free()
-    # the same run once more without the graph, for the per-stage split (captured events are not timed)
-    plan = fp.Plan(ix, len(allq), len(allq.chars), len(spec), tile_queries=opts["tile_queries"],
-                   variant=opts["variant"], graph=False)
-    r2 = plan.run(dq[0], dq[1], batches=spec)
-    split = {k_: r2.stats()[k_] for k_ in ("ms_prepare", "ms_filter", "ms_emit", "ms_total")}
-    r2.free()
-    plan.free()
+    hq = (torch.from_numpy(allq.chars).pin_memory().numpy(), torch.from_numpy(allq.offsets).pin_memory().numpy())
+    out = {}
+    rp = idx = None
+    for label, combined in (("combined", True), ("count32", False)):
+        ix = fp.fp_build(w.dictionary, fp_type="count", width=32, combined=combined)
+        opts = tune.tuned_plan_opts(ix, sample, batches=sspec, reps=1)
+        plan = fp.Plan(ix, len(allq), len(allq.chars), len(spec), tile_queries=opts["tile_queries"],
+                       variant=opts["variant"])
+        reps = 5 if combined else 2
+        ms, r = timed(lambda: plan.run(dq[0], dq[1], batches=spec), stream, flush, reps=reps, warm=1)
+        st = r.stats()
+        got = r.csr()
+        r.free()
+        e2e = None
+        if combined:
+            def through():
+                r_ = plan.run(hq[0], hq[1], batches=spec)
+                r_.csr(copy=False)
+                r_.free()
+            e2e = {"value": e2e_rate(through, len(allq), reps=2), "unit": "queries/s",
+                   "h2d_bytes": int(allq.chars.nbytes + allq.offsets.nbytes),
+                   "d2h_bytes": int(got[0].nbytes + got[1].nbytes)}
+        plan.free()
+        plan = fp.Plan(ix, len(allq), len(allq.chars), len(spec), tile_queries=opts["tile_queries"],
+                       variant=opts["variant"], graph=False)
+        r2 = plan.run(dq[0], dq[1], batches=spec)
+        split = {k_: r2.stats()[k_] for k_ in ("ms_prepare", "ms_filter", "ms_emit", "ms_total")}
+        r2.free()
+        plan.free()
+        ix.free()
+        if rp is None:
+            rp, idx = got
+        out[label] = {"tile": {k_: v for k_, v in opts.items() if k_ != "candidates"},
+                      "tile_candidates": opts.get("candidates"), "queries_per_s": len(allq) / (ms / 1e3),
+                      "pair_compares_per_s": st["pairs"] / (ms / 1e3), "ms": ms, "replays": reps,
+                      "pairs": st["pairs"], "survivors": st["survivors"], "matches": st["matches"],
+                      "rejection_rate": 1.0 - st["survivors"] / max(st["pairs"], 1),
+                      "stage_ms_without_graph": split, "identical_to_combined": same_csr((rp, idx), got)}
+        if e2e:
+            out[label]["e2e"] = e2e
     # oracle: two patterns of each of up to 8 batches per (k, metric) pair, one oracle call per pair
     picks = {}
     base = 0
     for b, (n, k, metric) in zip(batches, spec):
-        sel = picks.setdefault((k, metric), [])
-        if n and len(sel) < 16:
-            sel.extend({base, base + n - 1})
+        sel_ = picks.setdefault((k, metric), [])
+        if n and len(sel_) < 16:
+            sel_.extend({base, base + n - 1})
         base += n
     ok, checked = True, 0
     for (k, metric), rows in picks.items():
@@ -451,14 +732,16 @@ def batched_leg(fp, torch, args, stream, flush):
         for j, q in enumerate(rows):
             ok = ok and np.array_equal(idx[rp[q]:rp[q + 1]], oidx[orp[j]:orp[j + 1]])
             checked += 1
+    c = out["combined"]
     return {"batched": {
-        "workload": f"{len(w.dictionary):,} English-like words (lengths 2..64), count32; {len(spec)} batches, "
+        "workload": f"{len(w.dictionary):,} English-like words (lengths 2..64); {len(spec)} batches, "
                     f"{len(allq):,} patterns, sizes log-uniform 1..50,000, k in {{1, 2}}, Ham and Lev mixed",
-        "form": "one captured plan (fused filter + verify over every batch and length bucket), graph replay",
-        "tile": opts, "queries_per_s": len(allq) / (ms / 1e3), "pair_compares_per_s": st["pairs"] / (ms / 1e3),
-        "ms": ms, "pairs": st["pairs"], "survivors": st["survivors"], "matches": st["matches"],
-        "rejection_rate": 1.0 - st["survivors"] / max(st["pairs"], 1),
-        "stage_ms_without_graph": split,
+        "form": "one captured plan (fused filter + verify over every batch and length bucket), graph replay; "
+                "combined types (count32 + occ32) unless stated",
+        "tile": c["tile"], "queries_per_s": c["queries_per_s"], "pair_compares_per_s": c["pair_compares_per_s"],
+        "ms": c["ms"], "pairs": c["pairs"], "survivors": c["survivors"], "matches": c["matches"],
+        "rejection_rate": c["rejection_rate"], "stage_ms_without_graph": c["stage_ms_without_graph"],
+        "e2e": c.get("e2e"), "by_fingerprint": out,
         "oracle_checked_patterns": checked, "oracle_ok": bool(ok), "generation_s": gen_s}}
 
 
@@ -602,6 +885,18 @@ def main():
             result["cpu_baseline"] = cpu_baseline(w, args.cpu_sample)
         if rank == 0 and args.fp_type == "count":
             result["combined_types"] = combined_leg(fp, w, ix, dev, metrics, stream, flush, step_device, args)
+        if rank == 0:
+            result["fused_form"] = fused_leg(fp, ix, dev, metrics, stream, flush, step_device, args)
+        url_w = None
+        if rank == 0 and not args.no_small:
+            legs, url_w = small_legs(fp, torch, args, stream, flush, peak)
+            result.update(legs)
+            result["count_l1"] = count_l1_leg(fp, torch, w, stream, flush, peak)
+        if rank == 0 and not args.no_paper_cpu:
+            import oracle
+            oracle.build()
+            cases = [("english1m", w)] + ([("url2m", url_w)] if url_w is not None else [])
+            result["paper_method_cpu"] = paper_method_cpu(cases)
         if not args.no_url and rank == 0:
             result.update(url_legs(fp, torch, args, stream, flush))
         if not args.no_batched and rank == 0:

@@ -153,6 +153,7 @@ typedef struct {
     int64_t bucket_count[256]; /* words per length */
     int64_t device_bytes; /* device memory held by the index */
     int32_t qgram;        /* q of FP_QGRAM (1 for the other types) */
+    int32_t combined;     /* 1: combined types (fp_build_opts.combined) */
 } fp_index_info;
 
 typedef struct fp_index fp_index;

@@ -376,6 +376,7 @@ int fp_index_info_get(const fp_index *ix, fp_index_info *info) {
     for (int L = 0; L < 256; L++) info->bucket_count[L] = ix->h_count[L];
     info->device_bytes = ix->device_bytes;
     info->qgram = ix->P.q;
+    info->combined = ix->d_map2 != nullptr;
     return FP_OK;
 }
 

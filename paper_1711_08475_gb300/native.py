@@ -66,7 +66,7 @@ class fp_index_info(ctypes.Structure):
     _fields_ = [("n_words", ctypes.c_int64), ("type", ctypes.c_int32), ("width_bits", ctypes.c_int32),
                 ("count_bits", ctypes.c_int32), ("pos_bits", ctypes.c_int32), ("n_pos", ctypes.c_int32),
                 ("sigma", ctypes.c_int32), ("bucket_count", ctypes.c_int64 * 256),
-                ("device_bytes", ctypes.c_int64), ("qgram", ctypes.c_int32)]
+                ("device_bytes", ctypes.c_int64), ("qgram", ctypes.c_int32), ("combined", ctypes.c_int32)]
 
 
 class fp_probe_result(ctypes.Structure):

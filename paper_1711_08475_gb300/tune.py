@@ -2,8 +2,8 @@
 
 The cache is a JSON file (default: ~/.cache/fpmatch/autotune.json, or
 $FPMATCH_TUNE_CACHE) keyed by GPU model and SM count, library version,
-fingerprint type and width, k, metric, form, the dictionary size rounded to a
-power of two and the length mix of the pattern sample (its shares of seven
+fingerprint type, width, q-gram length and combined types, k, metric, form, the
+dictionary size rounded to a power of two and the length mix of the pattern sample (its shares of seven
 length classes, in tenths).  A miss runs fp_autotune on the given pattern
 sample.  tuned_plan_opts does the same for batched plans whose batches mix
 several (k, metric) pairs: it times every tile on a plan over the sample.
@@ -42,7 +42,8 @@ def _key(index, k, metric, mode, offsets) -> str:
     words = max(1, int(info["n_words"]))
     size = 1 << (words - 1).bit_length()
     return "|".join(str(x) for x in (props.name, props.multi_processor_count, fp_version(), info["type"],
-                                     info["width_bits"], info.get("qgram", 1), k, metric, mode, size,
+                                     info["width_bits"], info.get("qgram", 1), info.get("combined", 0), k, metric,
+                                     mode, size,
                                      length_mix(offsets)))
 
 
