@@ -457,6 +457,9 @@ FP_API const char *fp_version(void);
  *           compare with 2k) on register-resident operands; ops = pair tests
  *   kind 1: independent chains of 3-input logic operations; ops = LOP3s
  *   kind 2: independent chains of population counts; ops = POPCs
+ *   kind 3: the filter's k = 1 pattern loop (three XOR + POPC tests and one
+ *           ALU-only "at most two bits" test per pattern and thread, minimum,
+ *           hit mask, warp sum per 32 patterns), no pair passing; ops = pair tests
  * Every SM runs the same number of resident blocks; cycles come from the SM
  * clock counters, seconds from CUDA events on cuda_stream. */
 typedef struct {

@@ -5,7 +5,13 @@
 // register-resident dictionary fingerprints per thread, query fingerprints
 // read from shared memory, XOR + population count per pair, a minimum over
 // the eight, one compare with 2k.  kind 1 is independent chains of 3-input
-// logic operations, kind 2 independent chains of population counts.
+// logic operations, kind 2 independent chains of population counts.  kind 3
+// is the filter's own k = 1 pattern loop: four fingerprints per thread, three
+// through XOR + population count and one through the two-clear test, a
+// 3-input minimum, the sign of (minimum - 3) shifted into a 32-pattern hit
+// mask, patterns read four at a time from shared memory (128-bit loads), a
+// warp sum of the hits after every 32 patterns; the data never passes, so it
+// is the loop's ceiling without re-tests.
 // Each block reads its SM cycle counter before and after the loop, so the
 // rate per SM per clock needs no knowledge of the clock.
 #include <vector>
@@ -18,7 +24,7 @@ constexpr int PR_THREADS = 256;
 
 __global__ void __launch_bounds__(PR_THREADS) k_probe(int kind, int iters, uint32_t seed,
                                                      unsigned long long *cycles, uint32_t *sink) {
-    __shared__ uint32_t s_q[64];
+    __shared__ __align__(16) uint32_t s_q[64];
     const uint32_t t = blockIdx.x * PR_THREADS + threadIdx.x;
     if (threadIdx.x < 64) s_q[threadIdx.x] = (seed * 2654435761u) ^ (threadIdx.x * 0x9E3779B9u);
     __syncthreads();
@@ -57,7 +63,7 @@ __global__ void __launch_bounds__(PR_THREADS) k_probe(int kind, int iters, uint3
         }
 #pragma unroll
         for (int v = 0; v < 8; v++) acc ^= a[v];
-    } else {
+    } else if (kind == 2) {
         uint32_t a[8];
 #pragma unroll
         for (int v = 0; v < 8; v++) a[v] = w[v];
@@ -70,6 +76,28 @@ __global__ void __launch_bounds__(PR_THREADS) k_probe(int kind, int iters, uint3
         }
 #pragma unroll
         for (int v = 0; v < 8; v++) acc ^= a[v];
+    } else {
+        const uint4 *q4 = reinterpret_cast<const uint4 *>(s_q);
+        for (int it = 0; it < iters; it++) {
+            for (int jb = 0; jb < 64; jb += 32) {
+                uint32_t hits = 0;
+#pragma unroll
+                for (int jj = 0; jj < 32; jj += 4) {
+                    const uint4 q = q4[(jb + jj) >> 2];
+                    const uint32_t qs[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        const uint32_t f0 = __popc(w[0] ^ qs[u]), f1 = __popc(w[1] ^ qs[u]),
+                                       f2 = __popc(w[2] ^ qs[u]);
+                        const uint32_t x = w[3] ^ qs[u], t = x & (x - 1u), z = (t & (t - 1u)) | 2u;
+                        const uint32_t m = __vimin3_u32(f0, f1, min(f2, z));
+                        hits = __funnelshift_l(m - 3u, hits, 1);
+                    }
+                }
+                acc += __reduce_add_sync(0xffffffffu, __popc(hits));
+            }
+            w[0] ^= acc;
+        }
     }
     const long long c1 = clock64();
     if (threadIdx.x == 0) cycles[blockIdx.x] = (unsigned long long)(c1 - c0);
@@ -81,7 +109,7 @@ __global__ void __launch_bounds__(PR_THREADS) k_probe(int kind, int iters, uint3
 using namespace fpk;
 
 extern "C" int fp_probe(int kind, int iters, void *cuda_stream, fp_probe_result *out) {
-    if (!out || kind < 0 || kind > 2 || iters <= 0) return FP_E_INVAL;
+    if (!out || kind < 0 || kind > 3 || iters <= 0) return FP_E_INVAL;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     int per_sm = 0;
     FP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe, PR_THREADS, 0));
@@ -114,7 +142,7 @@ extern "C" int fp_probe(int kind, int iters, void *cuda_stream, fp_probe_result 
     double mean_cyc = 0;
     for (auto c : h) mean_cyc += (double)c;
     mean_cyc /= grid;
-    const double per_thread = (double)iters * 64.0 * 8.0;  // pair tests, LOP3s or POPCs
+    const double per_thread = (double)iters * 64.0 * (kind == 3 ? 4.0 : 8.0);  // pair tests, LOP3s or POPCs
     out->kind = kind;
     out->sm_count = sms;
     out->ops = per_thread * PR_THREADS * grid;
