@@ -172,3 +172,48 @@ def test_count_l1_parity(fp, english, urls, width, mode):
                 assert (st["pairs"], st["survivors"]) == (pairs, surv), (w.name, width, metric, k, mode)
                 # never more survivors than the Gray-coded count distance lets through
                 assert st["survivors"] <= fp.fp_query(gray_ix, Q, k=k, metric=metric).stats()["survivors"]
+
+
+# ---------------------------------------------------------------------------
+# full sizes: the bench's workloads, sampled
+# ---------------------------------------------------------------------------
+
+
+def full_sampled(fp, d, Q, ix, k, metric, dfp, qfp_of, kind, q, n_sample, seed):
+    """The whole batch through the bench's launch configuration: properties that
+    hold at any size, the match lists of sampled patterns against brute force,
+    and the sampled patterns' pairs passing the bound against the oracle's."""
+    res = fp.fp_query_ex(ix, Q, k=k, metric=metric)
+    rp, idx = res.csr()
+    assert rp[0] == 0 and np.all(np.diff(rp) >= 0) and rp[-1] == len(idx)
+    assert res.stats()["pairs"] == oracle.eligible_pairs(d, Q, k, metric)
+    sel = np.sort(datagen.permutation(datagen.stream_key(seed, "sample"), len(Q))[:n_sample])
+    sub = Q.subset(sel)
+    rp0, idx0, pairs0, surv0 = oracle.filter_match_fps(d, sub, k, metric, dfp, qfp_of(sub), kind, 32, q=q)
+    for j, qi in enumerate(sel):
+        assert np.array_equal(idx[rp[qi]:rp[qi + 1]], idx0[rp0[j]:rp0[j + 1]]), qi
+    st = fp.fp_query_ex(ix, sub, k=k, metric=metric).stats()
+    assert (st["pairs"], st["survivors"]) == (pairs0, surv0)
+
+
+def test_qgram_url2m_full_sampled(fp):
+    w = datagen.url2m()
+    d = w.dictionary
+    ix = fp.fp_build(d, fp_type="qgram", width=32, qgram=2)
+    grams, _ = oracle.qgram_map(d, 2, 32)
+    assert np.array_equal(ix.qgrams(), grams)
+    dfp = oracle.qgram_fingerprints(d, grams)
+    for metric in ("ham", "lev"):
+        full_sampled(fp, d, w.queries[metric], ix, 1, metric, dfp, lambda S: oracle.qgram_fingerprints(S, grams),
+                     "weight", 2, 40, 5)
+
+
+def test_count_l1_english1m_full_sampled(fp):
+    w = datagen.english1m()
+    d = w.dictionary
+    ix = fp.fp_build(d, fp_type="count_l1", width=32)
+    m = ix.symbol_map()
+    dfp = oracle.fingerprints(d, m, "count", 32, gray=False)
+    for metric in ("ham", "lev"):
+        full_sampled(fp, d, w.queries[metric], ix, 1, metric, dfp,
+                     lambda S: oracle.fingerprints(S, m, "count", 32, gray=False), "count_l1", 1, 60, 6)
