@@ -460,8 +460,11 @@ FP_API const char *fp_version(void);
  *   kind 3: the filter's k = 1 pattern loop (three XOR + POPC tests and one
  *           ALU-only "at most two bits" test per pattern and thread, minimum,
  *           hit mask, warp sum per 32 patterns), no pair passing; ops = pair tests
- * Every SM runs the same number of resident blocks; cycles come from the SM
- * clock counters, seconds from CUDA events on cuda_stream. */
+ * Every SM runs the same number of resident blocks.  ops_per_clk_per_sm
+ * divides the ops by each SM's span of cycles, from its first block's start
+ * to its last block's end (the blocks sharing an SM finish at different
+ * times, so one block's duration would understate the SM time); seconds come
+ * from CUDA events on cuda_stream, sm_clock_mhz = mean span / seconds. */
 typedef struct {
     int32_t kind;
     int32_t sm_count;

@@ -12,8 +12,14 @@
 // mask, patterns read four at a time from shared memory (128-bit loads), a
 // warp sum of the hits after every 32 patterns; the data never passes, so it
 // is the loop's ceiling without re-tests.
-// Each block reads its SM cycle counter before and after the loop, so the
-// rate per SM per clock needs no knowledge of the clock.
+// Each block records its SM's cycle counter before and after the loop and the
+// SM it ran on.  The blocks sharing an SM do not progress evenly (the warp
+// schedulers favour some of them, which finish early while the others still
+// run), so one block's own duration understates the SM time the blocks take
+// together; the rate per SM per clock is therefore taken over each SM's span,
+// from its first block's start to its last block's end (cycle counters are
+// per SM, so starts and ends compare within one SM only).
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
@@ -22,8 +28,15 @@ namespace fpk {
 
 constexpr int PR_THREADS = 256;
 
+__device__ __forceinline__ uint32_t sm_id() {
+    uint32_t s;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(s));
+    return s;
+}
+
+// rec[3 b .. 3 b + 2] = block b's start cycle, end cycle and SM
 __global__ void __launch_bounds__(PR_THREADS) k_probe(int kind, int iters, uint32_t seed,
-                                                     unsigned long long *cycles, uint32_t *sink) {
+                                                     unsigned long long *rec, uint32_t *sink) {
     __shared__ __align__(16) uint32_t s_q[64];
     const uint32_t t = blockIdx.x * PR_THREADS + threadIdx.x;
     if (threadIdx.x < 64) s_q[threadIdx.x] = (seed * 2654435761u) ^ (threadIdx.x * 0x9E3779B9u);
@@ -100,7 +113,11 @@ __global__ void __launch_bounds__(PR_THREADS) k_probe(int kind, int iters, uint3
         }
     }
     const long long c1 = clock64();
-    if (threadIdx.x == 0) cycles[blockIdx.x] = (unsigned long long)(c1 - c0);
+    if (threadIdx.x == 0) {
+        rec[3 * blockIdx.x + 0] = (unsigned long long)c0;
+        rec[3 * blockIdx.x + 1] = (unsigned long long)c1;
+        rec[3 * blockIdx.x + 2] = sm_id();
+    }
     if (acc == 0x12345678u) sink[t] = acc;
 }
 
@@ -118,7 +135,7 @@ extern "C" int fp_probe(int kind, int iters, void *cuda_stream, fp_probe_result 
     const int grid = sms * per_sm;
     unsigned long long *cyc = nullptr;
     uint32_t *sink = nullptr;
-    FP_CUDA(cudaMalloc((void **)&cyc, sizeof(unsigned long long) * grid));
+    FP_CUDA(cudaMalloc((void **)&cyc, sizeof(unsigned long long) * 3 * grid));
     FP_CUDA(cudaMalloc((void **)&sink, sizeof(uint32_t) * grid * PR_THREADS));
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -132,23 +149,38 @@ extern "C" int fp_probe(int kind, int iters, void *cuda_stream, fp_probe_result 
     cudaError_t e = cudaEventSynchronize(e1);
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
-    std::vector<unsigned long long> h(grid);
-    if (e == cudaSuccess) e = cudaMemcpy(h.data(), cyc, sizeof(unsigned long long) * grid, cudaMemcpyDeviceToHost);
+    std::vector<unsigned long long> h(3 * (size_t)grid);
+    if (e == cudaSuccess) e = cudaMemcpy(h.data(), cyc, sizeof(unsigned long long) * 3 * grid, cudaMemcpyDeviceToHost);
     cudaFree(cyc);
     cudaFree(sink);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (e != cudaSuccess) return cuda_fail(e, "fp_probe");
-    double mean_cyc = 0;
-    for (auto c : h) mean_cyc += (double)c;
-    mean_cyc /= grid;
+    // per SM: blocks, first start, last end
+    std::vector<long long> nblk(sms, 0);
+    std::vector<unsigned long long> first(sms, ~0ull), last(sms, 0);
+    for (int b = 0; b < grid; b++) {
+        const unsigned long long sm = h[3 * b + 2];
+        if (sm >= (unsigned long long)sms) return fail(FP_E_CUDA, "fp_probe: SM id out of range");
+        nblk[sm]++;
+        first[sm] = std::min(first[sm], h[3 * b]);
+        last[sm] = std::max(last[sm], h[3 * b + 1]);
+    }
+    double blocks = 0, span = 0;  // over the SMs that ran blocks
+    int used = 0;
+    for (int i = 0; i < sms; i++)
+        if (nblk[i]) {
+            blocks += (double)nblk[i];
+            span += (double)(last[i] - first[i]);
+            used++;
+        }
     const double per_thread = (double)iters * 64.0 * (kind == 3 ? 4.0 : 8.0);  // pair tests, LOP3s or POPCs
     out->kind = kind;
     out->sm_count = sms;
     out->ops = per_thread * PR_THREADS * grid;
     out->seconds = ms * 1e-3;
     out->ops_per_s = out->ops / out->seconds;
-    out->ops_per_clk_per_sm = per_thread * PR_THREADS * per_sm / mean_cyc;
-    out->sm_clock_mhz = mean_cyc / out->seconds * 1e-6;
+    out->ops_per_clk_per_sm = per_thread * PR_THREADS * blocks / span;  // ops per SM-cycle of the spans
+    out->sm_clock_mhz = used ? span / used / out->seconds * 1e-6 : 0.0;
     return FP_OK;
 }
