@@ -336,7 +336,7 @@ int fp_build(const uint8_t *chars, const int64_t *offsets, int64_t n_words, int 
         goto fail_out;
     }
     ix->device_bytes = ix->D.n_slots * (4 + 1 + 4) + (ix->D.n_slots + FP_SLACK_SLOTS) * (P.width / 8) +
-                       ix->D.str_bytes + STR_SLACK + 256 * 9 + (ix->D.fp2 ? ix->D.n_slots * 4 + 256 : 0) +
+                       ix->D.str_bytes + STR_SLACK + 256 * 9 + (ix->D.fp2 ? (ix->D.n_slots + FP_SLACK_SLOTS) * 4 + 256 : 0) +
                        (ix->d_wstart ? 256 * 4 * (int64_t)(cell_count(P.width) + 1) : 0) +
                        (ix->d_gmap ? (int64_t)1 << (8 * P.q) : 0);
     S.release(st);

@@ -854,10 +854,14 @@ __global__ void __launch_bounds__(256) k_second_fp(Bucketed B, const int8_t *__r
 
 int second_fingerprints(Bucketed *B, const int8_t *d_map2, const FpParams &P2, cudaStream_t st) {
     if (!B->fp2) {
-        const size_t bytes = sizeof(uint32_t) * (size_t)(B->n_slots > 0 ? B->n_slots : 1);
+        // readable slack after the last slot, as for the first fingerprints: the
+        // filter reads a lane's four slots with one 128-bit load
+        const size_t bytes = sizeof(uint32_t) * ((size_t)(B->n_slots > 0 ? B->n_slots : 0) + FP_SLACK_SLOTS);
         const cudaError_t e = B->stream_ordered ? cudaMallocAsync((void **)&B->fp2, bytes, st)
                                                 : cudaMalloc((void **)&B->fp2, bytes);
         if (e != cudaSuccess) return cuda_fail(e, "second fingerprints");
+        const cudaError_t z = cudaMemsetAsync(B->fp2, 0, bytes, st);
+        if (z != cudaSuccess) return cuda_fail(z, "second fingerprints");
     }
     if (B->n_slots <= 0) return FP_OK;
     k_second_fp<<<grid_for(B->n_slots, 256, 8192), 256, 0, st>>>(*B, d_map2, P2);

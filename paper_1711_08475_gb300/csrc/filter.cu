@@ -242,6 +242,23 @@ __device__ __forceinline__ void all_fd(const uint32_t (&w)[V], uint32_t q, const
     }
 }
 
+// Combined types: bit i = fingerprint i of lane src (W = 32, so fingerprint
+// i is slot wbase + (i/4)*128 + src*4 + i%4) has a second fingerprint within
+// 2k of the pattern's second fingerprint q2 (Eq. 1 on the 32-bit occurrence
+// fingerprints).  Four slots per 128-bit load: the dictionary's second
+// fingerprints carry readable slack past the last slot, like its first.
+template <int V>
+__device__ __forceinline__ uint32_t second_pass(const uint32_t *dfp2, uint32_t wbase, int src, uint32_t q2, uint32_t T2) {
+    uint32_t bits = 0;
+#pragma unroll
+    for (int r = 0; r < V / 4; r++) {
+        const uint4 x = *reinterpret_cast<const uint4 *>(dfp2 + wbase + r * 128 + src * 4);
+        bits |= ((uint32_t)(__popc(x.x ^ q2) <= T2) | (uint32_t)(__popc(x.y ^ q2) <= T2) << 1 |
+                 (uint32_t)(__popc(x.z ^ q2) <= T2) << 2 | (uint32_t)(__popc(x.w ^ q2) <= T2) << 3) << (4 * r);
+    }
+    return bits;
+}
+
 // Moves the warp's staged survivors to the global list (one reservation).
 __device__ __forceinline__ void flush_stage(const FilterArgs &A, uint64_t *stage, uint32_t *cnt, int lane) {
     __syncwarp();
@@ -383,7 +400,8 @@ __device__ __forceinline__ void make_room(const FilterArgs &A, uint64_t *stage, 
 // shuffles and stages every pair of that query and those fingerprints that
 // passes Eq. 1.
 template <int W, int V, int FDK, bool FULL, bool FUSED, bool COMB>
-__device__ __forceinline__ void retest_round(const FilterArgs &A, const uint32_t *s_q, const uint16_t *queue,
+__device__ __forceinline__ void retest_round(const FilterArgs &A, const uint32_t *s_q, const uint32_t *s_q2,
+                                             const uint16_t *queue,
                                              uint32_t first, uint32_t count, uint32_t q0, const uint32_t (&w)[V],
                                              uint32_t invalid, uint32_t T, uint32_t wbase, uint64_t *stage,
                                              uint32_t *cnt, int lane, int k, int metric) {
@@ -400,11 +418,17 @@ __device__ __forceinline__ void retest_round(const FilterArgs &A, const uint32_t
     if (has) {
         uint32_t F[NF];
         all_fd<W, V, FDK, NF>(ws, s_q[jq], A.M, F);
+        uint32_t pass = 0;
+#pragma unroll
+        for (int i = 0; i < NF; i++) pass |= (uint32_t)(F[i] <= T) << i;
+        if (!FULL) pass &= ~inv;
+        // combined types: the second check for the whole round's fingerprints at once
+        if (COMB && pass) pass &= second_pass<V>(A.dfp2, wbase, src, s_q2[jq], 2u * (uint32_t)k);
 #pragma unroll
         for (int i = 0; i < NF; i++)
-            if (F[i] <= T && (FULL || !((inv >> i) & 1u)))
-                stage_push<FUSED, COMB>(A, stage, cnt, ((uint64_t)(q0 + jq) << 32) | (uint64_t)(wbase + lane_offset<G>(i, src)),
-                                  k, metric);
+            if ((pass >> i) & 1u)
+                stage_push<FUSED, false>(A, stage, cnt, ((uint64_t)(q0 + jq) << 32) | (uint64_t)(wbase + lane_offset<G>(i, src)),
+                                         k, metric);
     }
 }
 
@@ -420,7 +444,8 @@ __device__ __forceinline__ void retest_round(const FilterArgs &A, const uint32_t
 // full round, so nearly every round keeps all 32 lanes busy; the last partial
 // round runs when the tile ends (the fingerprints in registers belong to it).
 template <int W, int V, int FDK, bool FULL, bool K1MIX, bool FUSED, bool COMB>
-__device__ __forceinline__ void scan_tile(const FilterArgs &A, const uint32_t *s_q, uint32_t nq, uint32_t q0,
+__device__ __forceinline__ void scan_tile(const FilterArgs &A, const uint32_t *s_q, const uint32_t *s_q2, uint32_t nq,
+                                          uint32_t q0,
                                           const uint32_t (&w)[V], uint32_t invalid, uint32_t T, uint32_t wbase,
                                           uint64_t *stage, uint32_t *cnt, uint16_t *queue, uint32_t *qcnt, int lane,
                                           int k, int metric) {
@@ -456,7 +481,7 @@ __device__ __forceinline__ void scan_tile(const FilterArgs &A, const uint32_t *s
             uint32_t done = 0;
             for (; qn - done >= 32u; done += 32u) {
                 make_room<NF, FUSED>(A, stage, cnt, lane, k, metric);
-                retest_round<W, V, FDK, FULL, FUSED, COMB>(A, s_q, queue, done, 32u, q0, w, invalid, T, wbase, stage, cnt,
+                retest_round<W, V, FDK, FULL, FUSED, COMB>(A, s_q, s_q2, queue, done, 32u, q0, w, invalid, T, wbase, stage, cnt,
                                                      lane, k, metric);
             }
             if (done) {  // move the rest (< 32) to the front
@@ -478,10 +503,15 @@ __device__ __forceinline__ void scan_tile(const FilterArgs &A, const uint32_t *s
                 if (mine) {
                     uint32_t F[NF];
                     all_fd<W, V, FDK, NF>(w, s_q[jb + jj], A.M, F);
+                    uint32_t pass = 0;
+#pragma unroll
+                    for (int i = 0; i < NF; i++) pass |= (uint32_t)(F[i] <= T) << i;
+                    if (!FULL) pass &= ~invalid;
+                    if (COMB && pass) pass &= second_pass<V>(A.dfp2, wbase, lane, s_q2[jb + jj], 2u * (uint32_t)k);
 #pragma unroll
                     for (int i = 0; i < NF; i++)
-                        if (F[i] <= T && (FULL || !((invalid >> i) & 1u)))
-                            stage_push<FUSED, COMB>(
+                        if ((pass >> i) & 1u)
+                            stage_push<FUSED, false>(
                                 A, stage, cnt,
                                 ((uint64_t)(q0 + jb + jj) << 32) | (uint64_t)(wbase + lane_offset<G>(i, lane)), k, metric);
                 }
@@ -497,7 +527,7 @@ __device__ __forceinline__ void scan_tile(const FilterArgs &A, const uint32_t *s
     const uint32_t qn = *qcnt;
     if (qn) {
         make_room<NF, FUSED>(A, stage, cnt, lane, k, metric);
-        retest_round<W, V, FDK, FULL, FUSED, COMB>(A, s_q, queue, 0u, qn, q0, w, invalid, T, wbase, stage, cnt, lane, k,
+        retest_round<W, V, FDK, FULL, FUSED, COMB>(A, s_q, s_q2, queue, 0u, qn, q0, w, invalid, T, wbase, stage, cnt, lane, k,
                                              metric);
         __syncwarp();
         if (lane == 0) *qcnt = 0;
@@ -528,6 +558,7 @@ __global__ void __launch_bounds__(FT_THREADS, (ft_min_blocks<W, V, FDK, FUSED>()
     constexpr int CW = NF * 32;                      // fingerprints per column
     constexpr int TW = CW * FT_WARPS * FT_COLS;      // fingerprints per tile
     __shared__ __align__(16) uint32_t s_q[FT_MAX_TQ];
+    __shared__ uint32_t s_q2[COMB ? FT_MAX_TQ : 1];  // combined types: the patterns' second fingerprints
     __shared__ uint64_t s_stage[FT_WARPS][FT_STAGE];
     __shared__ uint32_t s_cnt[FT_WARPS];
     __shared__ uint16_t s_queue[FT_WARPS][FT_QUEUE];
@@ -560,6 +591,7 @@ __global__ void __launch_bounds__(FT_THREADS, (ft_min_blocks<W, V, FDK, FUSED>()
             for (uint32_t j = lane; j < nq; j += 32) {
                 uint32_t f = (W == 32) ? A.qfp32[q0 + j] : (uint32_t)A.qfp16[q0 + j];
                 s_q[j] = (W == 32) ? f : (f | (f << 16));
+                if (COMB) s_q2[j] = A.qfp2[q0 + j];
             }
             if (lane == 0) s_seg = S;
         }
@@ -599,10 +631,10 @@ __global__ void __launch_bounds__(FT_THREADS, (ft_min_blocks<W, V, FDK, FUSED>()
                 if (lane_offset<G>(i, lane) >= nvalid) invalid |= 1u << i;
             const uint32_t qa = b0 * 32u, qn = min(nq, b1 * 32u) - qa;
             if (K1MIX && T != 2u)  // a k = 1 variant given another k: exact general path
-                scan_tile<W, V, FDK, false, false, FUSED, COMB>(A, s_q + qa, qn, q0 + qa, w, invalid, T, wbase, stage,
+                scan_tile<W, V, FDK, false, false, FUSED, COMB>(A, s_q + qa, s_q2 + (COMB ? qa : 0u), qn, q0 + qa, w, invalid, T, wbase, stage,
                                                                 cnt, queue, qcnt, lane, k, metric);
             else
-                scan_tile<W, V, FDK, false, K1MIX, FUSED, COMB>(A, s_q + qa, qn, q0 + qa, w, invalid, T, wbase, stage,
+                scan_tile<W, V, FDK, false, K1MIX, FUSED, COMB>(A, s_q + qa, s_q2 + (COMB ? qa : 0u), qn, q0 + qa, w, invalid, T, wbase, stage,
                                                                 cnt, queue, qcnt, lane, k, metric);
             it += b1 - b0;
         }
