@@ -42,8 +42,9 @@ constexpr int FT_QUEUE = 256;  // queued (lane, tile query) hits per warp
 // Resident blocks per SM the register budget is set for (blocks of 128
 // threads): the 32-bit, 4-words-per-thread filter fits 32 registers (16
 // blocks, 64 warps); the other shapes keep 48 (10 blocks); the fused form,
-// which calls the verifier, is fastest at 64 registers (8 blocks; a few
-// spills).  Four-warp blocks beat eight-warp ones by 1-2 %: fewer warps wait
+// which calls the verifier, is fastest at 80 registers (6 blocks, no spills
+// to speak of): 13 % faster than 8 blocks at 64 registers on mixed k = 1, 2
+// batches, and 10 blocks or more spill hundreds of bytes.  Four-warp blocks beat eight-warp ones by 1-2 %: fewer warps wait
 // at a tile's barrier for the slowest one.
 #ifndef FT_MIN_BLOCKS
 #define FT_MIN_BLOCKS 10
@@ -52,7 +53,7 @@ constexpr int FT_QUEUE = 256;  // queued (lane, tile query) hits per warp
 #define FT_MAIN_MIN_BLOCKS 16
 #endif
 #ifndef FT_FUSED_MIN_BLOCKS
-#define FT_FUSED_MIN_BLOCKS 8
+#define FT_FUSED_MIN_BLOCKS 6
 #endif
 #ifndef FT_MIX_DIV
 #define FT_MIX_DIV 4  // k = 1 mix: V / FT_MIX_DIV of a thread's words use the ALU-only test
