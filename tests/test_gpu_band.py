@@ -145,6 +145,67 @@ def test_batched_plan_falls_back_to_whole_buckets(fp):
             base += n
 
 
+def short_words_twenty_letters():
+    """Every word of length 1..3 over twenty letters (8,420 words) and, as
+    patterns, every 23rd word of length 2..3 (366, deterministic, no draw).  The
+    count fingerprint tracks 16 of the letters, the occurrence fingerprint all
+    twenty, so the second check has letters of its own to reject on."""
+    import itertools
+    words = [bytes(t) for n in range(1, 4) for t in itertools.product(b"etaoinshrdlucmfwypvg", repeat=n)]
+    d = datagen.Strings.from_list(words)
+    rows = np.nonzero(d.lengths() >= 2)[0][::23]
+    return d, d.subset(rows)
+
+
+@pytest.mark.parametrize("mode", ["tiled", "fused"])
+def test_combined_types_dense_batches(fp, mode):
+    """Combined types where most pairs pass the first fingerprint: short words
+    have fingerprints of few bits, so at k = 2 about 60 % of the eligible pairs
+    pass count32 alone and most 32-pattern batches hold more passing (lane,
+    pattern) cells than the hit queue; they take the one-pattern-at-a-time path,
+    which checks the second fingerprints there.  Match lists equal the oracle's
+    and the survivors are exactly the pairs whose two fingerprints both pass
+    Eq. 1."""
+    d, q = short_words_twenty_letters()
+    ix = fp.fp_build(d, fp_type="count", width=32, combined=True)
+    plain = fp.fp_build(d, fp_type="count", width=32)
+    mc = ix.symbol_map()
+    mo, _, _ = oracle.default().symbol_map(d.chars, "common", 32)
+    fd = (oracle.fingerprints(d, mc, "count", 32).astype(np.uint64), oracle.fingerprints(d, mo, "occ", 32).astype(np.uint64))
+    fq = (oracle.fingerprints(q, mc, "count", 32).astype(np.uint64), oracle.fingerprints(q, mo, "occ", 32).astype(np.uint64))
+    for metric, k in (("lev", 2), ("ham", 2), ("lev", 1)):
+        r = fp.fp_query_ex(ix, q, k=k, metric=metric, mode=mode)
+        rp0, idx0 = oracle.match(d, q, k, metric)
+        rp, idx = r.csr()
+        assert np.array_equal(rp, rp0) and np.array_equal(idx, idx0), (mode, metric, k)
+        st = r.stats()
+        assert st["survivors"] == pair_survivors(d, q, k, metric, fd, fq), (mode, metric, k)
+        # dense: most eligible pairs pass the count fingerprint alone
+        st1 = fp.fp_query_ex(plain, q, k=k, metric=metric, mode=mode).stats()
+        assert st1["survivors"] == pair_survivors(d, q, k, metric, fd[:1], fq[:1])
+        if k == 2:
+            assert st1["survivors"] > 0.5 * st1["pairs"], (metric, st1)
+        assert st["survivors"] < st1["survivors"]
+
+
+def test_combined_types_dense_plan(fp):
+    """The same dense workload through one captured plan with (k, metric) groups
+    mixed, replayed once: every group's rows are the oracle's."""
+    d, q = short_words_twenty_letters()
+    ix = fp.fp_build(d, fp_type="count", width=32, combined=True)
+    n = len(q)
+    cut = [0, n // 3, 2 * n // 3, n]
+    spec = [(cut[1] - cut[0], 2, "lev"), (cut[2] - cut[1], 1, "ham"), (cut[3] - cut[2], 2, "ham")]
+    plan = fp.Plan(ix, n, len(q.chars), len(spec))
+    for _ in range(2):  # capture, then replay
+        rp, idx = plan.run(q, batches=spec).csr()
+        for (m, k, metric), lo in zip(spec, cut):
+            rp0, idx0 = oracle.match(d, q.subset(np.arange(lo, lo + m)), k, metric)
+            assert np.array_equal(rp[lo:lo + m + 1] - rp[lo], rp0), (k, metric)
+            assert np.array_equal(idx[rp[lo]:rp[lo + m]], idx0), (k, metric)
+    plan.free()
+
+
 def pair_survivors(d, q, k, metric, fps_d, fps_q):
     """Eligible pairs whose every fingerprint pair passes Eq. 1 (popc(x) <= 2k)."""
     ld, lq = d.lengths(), q.lengths()
