@@ -41,11 +41,12 @@ constexpr int FT_QUEUE = 256;  // queued (lane, tile query) hits per warp
 // Tuning constants (compile-time; the defaults come from sweeps on GB300).
 // Resident blocks per SM the register budget is set for (blocks of 128
 // threads): the 32-bit, 4-words-per-thread filter fits 32 registers (16
-// blocks, 64 warps); the other shapes keep 48 (10 blocks); the fused form,
-// which calls the verifier, is fastest at 80 registers (6 blocks, no spills
-// to speak of): 13 % faster than 8 blocks at 64 registers on mixed k = 1, 2
-// batches, and 10 blocks or more spill hundreds of bytes.  Four-warp blocks beat eight-warp ones by 1-2 %: fewer warps wait
-// at a tile's barrier for the slowest one.
+// blocks, 64 warps); 32-bit position fingerprints take 64 (8 blocks); the
+// other shapes keep 48 (10 blocks); the fused form, which calls the verifier,
+// is fastest at 80 registers (6 blocks, no spills to speak of): 13 % faster
+// than 8 blocks at 64 registers on mixed k = 1, 2 batches, and 10 blocks or
+// more spill hundreds of bytes.  Four-warp blocks beat eight-warp ones by
+// 1-2 %: fewer warps wait at a tile's barrier for the slowest one.
 #ifndef FT_MIN_BLOCKS
 #define FT_MIN_BLOCKS 10
 #endif
@@ -54,6 +55,9 @@ constexpr int FT_QUEUE = 256;  // queued (lane, tile query) hits per warp
 #endif
 #ifndef FT_FUSED_MIN_BLOCKS
 #define FT_FUSED_MIN_BLOCKS 6
+#endif
+#ifndef FT_POS_MIN_BLOCKS
+#define FT_POS_MIN_BLOCKS 8  // 32-bit position fingerprints: 7 % faster than at 10 (the 16-bit shapes are not)
 #endif
 #ifndef FT_MIX_DIV
 #define FT_MIX_DIV 4  // k = 1 mix: V / FT_MIX_DIV of a thread's words use the ALU-only test
@@ -538,7 +542,9 @@ __device__ __forceinline__ void scan_tile(const FilterArgs &A, const uint32_t *s
 
 template <int W, int V, int FDK, bool FUSED>
 constexpr int ft_min_blocks() {
-    return FUSED ? FT_FUSED_MIN_BLOCKS : ((W == 32 && V == 4 && FDK == FDK_POPC) ? FT_MAIN_MIN_BLOCKS : FT_MIN_BLOCKS);
+    return FUSED ? FT_FUSED_MIN_BLOCKS
+                 : ((W == 32 && V == 4 && FDK == FDK_POPC) ? FT_MAIN_MIN_BLOCKS
+                                                           : ((W == 32 && FDK == FDK_POS) ? FT_POS_MIN_BLOCKS : FT_MIN_BLOCKS));
 }
 
 // W: fingerprint width; V: 32-bit words per thread (multiple of 4).
